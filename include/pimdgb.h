@@ -1,0 +1,166 @@
+/*
+ * pimdgb: batched Born-Oppenheimer energies and forces of every replica of a
+ * replica-parallel ab initio simulation step, on one GB300 (sm_103a).
+ *
+ * The paper (arXiv:1601.02713, Sec. 2) states the problem this library
+ * solves: a PIMD (or string-method) step produces n nuclear configurations
+ * (replicas: beads or images); the Born-Oppenheimer energy and forces of each
+ * replica are computed, gathered, and the driver moves the replicas. Each
+ * energy/force here is a closed-shell restricted Hartree-Fock (RHF) direct SCF
+ * in a contracted Gaussian basis: Schwarz-screened electron-repulsion integrals
+ * contracted into Coulomb and exchange matrices, Pulay DIIS, diagonalisation,
+ * then the analytic gradient from derivative integrals. Integral cutoff 1e-12
+ * as in Sec. 3.1. All replicas of a call are evaluated together, ragged sizes
+ * included, so a call is the whole force step of the paper's Fig. 1(a).
+ *
+ * Conventions
+ *   units: coordinates in bohr, energies in hartree, gradients dE/dR in
+ *          hartree/bohr (the force is minus the gradient);
+ *   charge 0, closed shell (the electron count sum(Z) must be even);
+ *   all array arguments of the host entry points are caller-owned HOST memory,
+ *   read before the call returns; outputs are written before it returns
+ *   (the call synchronises its stream);
+ *   the *_dev entry points take DEVICE pointers (caller-owned, on the device of
+ *   the context) and a cudaStream_t passed as void*; they return after the
+ *   results are in the caller's device buffers (the stream is synchronised).
+ *   Errors are negative return codes (pimd_strerror gives a message); on error
+ *   outputs are unspecified except for PIMD_ENOTCONV (see below).
+ *   A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef PIMDGB_H
+#define PIMDGB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIMD_OK 0
+#define PIMD_EINVAL -1     /* bad argument: sizes, NaN coordinates, element missing from basis, odd electrons */
+#define PIMD_ENOMEM -2     /* device allocation failed */
+#define PIMD_ECUDA -3      /* CUDA runtime error */
+#define PIMD_ENOTCONV -4   /* some replica's SCF did not converge in max_iter; outputs written, info flags it */
+#define PIMD_ETIMEOUT -5   /* a bounded device wait expired */
+#define PIMD_EBASIS -6     /* overlap matrix numerically singular (min eigenvalue < 1e-8) */
+
+typedef struct pimd_ctx pimd_ctx;
+typedef struct pimd_basis pimd_basis;
+
+/* SCF options. struct_size must be sizeof(pimd_scf_opts); fields added later
+ * go at the end. pimd_scf_opts_default fills the defaults shown. */
+typedef struct {
+    size_t struct_size;
+    double conv_energy;   /* |E_k - E_{k-1}| threshold, 1e-10 hartree */
+    double conv_error;    /* max |X^T (FDS - SDF) X| threshold, 1e-8 */
+    int max_iter;         /* 64 */
+    int diis_size;        /* 8 (Pulay subspace, 2..8) */
+    double schwarz_tau;   /* 1e-12: quartets with Q_ab Q_cd below it are skipped (Sec. 3.1) */
+    double fp32_tau;      /* 0: all quartets in FP64 */
+    int guess;            /* 0 core Hamiltonian, 1 previous MOs of the same replica index (Sec. 2:
+                             MOs of each replica reused as the next step's guess), falls back to 0 */
+    int deterministic;    /* reserved, 0 */
+    int want_gradient;    /* 1 */
+} pimd_scf_opts;
+
+/* Per-replica result record. */
+typedef struct {
+    int iterations;       /* SCF iterations (Fock builds) */
+    int converged;        /* 1 if both thresholds were met */
+    double final_dE;      /* last |E_k - E_{k-1}| */
+    double final_error;   /* last max |X^T (FDS - SDF) X| */
+    long long nquartets;  /* screened shell quartets per Fock build */
+} pimd_info;
+
+void pimd_scf_opts_default(pimd_scf_opts* opts);
+
+/* Create a context on CUDA device `device` (owns streams, workspaces, the
+ * Boys table and the per-replica MO cache). Returns 0 or an error. */
+int pimd_ctx_create(pimd_ctx** out, int device);
+void pimd_ctx_destroy(pimd_ctx* ctx);
+
+/* Basis set, per element (immutable after creation).
+ *   nelem            number of elements described;
+ *   Z_of_elem[e]     nuclear charge of element e (1..118, distinct);
+ *   nshell_of_elem[e] number of contracted shells of element e;
+ *   shell_l[s], shell_nprim[s]  angular momentum (0..2) and primitive count
+ *                    (1..3) of shell s, shells of element 0 first, then 1, ...;
+ *   exps, coefs      primitive exponents and raw contraction coefficients of
+ *                    every shell in order (coefficients multiply normalised
+ *                    primitives; the library normalises each contraction);
+ *   spherical        1: d shells are the 5 real solid harmonics (m = -2..2:
+ *                    sqrt3 xy, sqrt3 yz, zz-(xx+yy)/2, sqrt3 xz, sqrt3/2 (xx-yy));
+ *                    0 is rejected (PIMD_EINVAL) in this version.
+ * Within a shell, p functions are ordered x, y, z. */
+int pimd_basis_create(pimd_basis** out, int nelem, const int* Z_of_elem, const int* nshell_of_elem,
+                      const int* shell_l, const int* shell_nprim, const double* exps, const double* coefs,
+                      int spherical);
+void pimd_basis_destroy(pimd_basis* basis);
+
+/* Number of basis functions of a molecule with the given charges. */
+int pimd_basis_nbf(const pimd_basis* basis, int natom, const int* Z);
+
+/* PIMD beads (Sec. 2, Fig. 1(a)): nrep replicas of the same molecule.
+ *   Z[natom], coords[nrep][natom][3] (bohr)  -> energies[nrep] (hartree),
+ *   gradients[nrep][natom][3] (hartree/bohr; may be NULL if opts->want_gradient == 0),
+ *   info[nrep] (may be NULL). opts may be NULL (defaults). */
+int pimd_bo_forces(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
+                   const pimd_basis* basis, const pimd_scf_opts* opts, double* energies, double* gradients,
+                   pimd_info* info);
+
+/* String-method images (Sec. 3.2): nimg replicas of different sizes.
+ *   natom_of_img[nimg]; Z_concat and coords_concat ([sum natom][3], bohr)
+ *   hold the images one after another; gradients_concat is laid out the same. */
+int string_images_forces(pimd_ctx* ctx, int nimg, const int* natom_of_img, const int* Z_concat,
+                         const double* coords_concat, const pimd_basis* basis, const pimd_scf_opts* opts,
+                         double* energies, double* gradients_concat, pimd_info* info);
+
+/* Device-pointer variants: Z and natom_of_img stay HOST arrays (they fix the
+ * work layout); coords, energies and gradients are DEVICE pointers; stream is
+ * a cudaStream_t (NULL: the context's stream). */
+int pimd_bo_forces_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords_dev,
+                       const pimd_basis* basis, const pimd_scf_opts* opts, double* energies_dev,
+                       double* gradients_dev, pimd_info* info, void* stream);
+int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* natom_of_img, const int* Z_concat,
+                             const double* coords_concat_dev, const pimd_basis* basis, const pimd_scf_opts* opts,
+                             double* energies_dev, double* gradients_concat_dev, pimd_info* info, void* stream);
+
+/* Drop the cached MOs (guess = 1 then starts from the core Hamiltonian). */
+void pimd_ctx_clear_guess(pimd_ctx* ctx);
+
+/* Launch statistics of the last forces call: kernels launched, Fock builds,
+ * and the device time (ms, CUDA events on the context stream) of the ERI
+ * Fock-build kernels, of the two-electron gradient kernels and of the whole call. */
+typedef struct {
+    long long kernel_launches;
+    int fock_builds;
+    double ms_fock;
+    double ms_grad2e;
+    double ms_total;
+    long long nquartets_total;   /* screened quartets over all replicas, per Fock build */
+    double eri_flops_per_build;  /* counted FP64 operations of the VRR per Fock build (all replicas) */
+} pimd_stats;
+int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
+
+/* Testing hooks (same kernels as the forces path):
+ * pimd_fock_dev: for nrep replicas of one molecule and a given density
+ *   D[nrep][N][N] (device), write G = J - K/2 (device, [nrep][N][N]) with
+ *   J_mn = sum D_ls (mn|ls), K_mn = sum D_ls (ml|ns).
+ * pimd_one_electron: S, T, V matrices of one molecule (host arrays [N][N]). */
+int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords, const pimd_basis* basis,
+                  double schwarz_tau, const double* D_dev, double* G_dev);
+int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coords, const pimd_basis* basis,
+                      double* S, double* T, double* V);
+int pimd_boys_dev(pimd_ctx* ctx, int n, int m, const double* T_dev, double* F_dev);
+
+/* Roofline denominators measured on the device: FP64 FMA, FP32 FMA and FP64
+ * tensor-core MMA throughput in TFLOP/s (bounded microbenchmarks, ~1 s). Any
+ * output pointer may be NULL. No counterpart in the paper (measurement aid). */
+int pimd_peak_bench(int device, double* fp64_tflops, double* fp32_tflops, double* dmma_tflops);
+
+const char* pimd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

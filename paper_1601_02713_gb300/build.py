@@ -1,0 +1,283 @@
+"""Build the CUDA library `_build/libpimdgb.so` for sm_103a.
+
+Steps: run the ERI code generator (csrc/gen_eri.py) into `_build/gen`, write
+one translation unit per quartet class (Fock build + Schwarz, and gradient)
+plus a dispatch table, compile every unit with nvcc in parallel, link a shared
+library. Object files are cached by a hash of their inputs and flags.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import importlib.util
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+GEN = os.path.join(BUILD, "gen")
+OBJ = os.path.join(BUILD, "obj")
+LIB = os.path.join(BUILD, "libpimdgb.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+         "-Xptxas", "-warn-spills", "-w", "-I" + CSRC, "-I" + GEN, "-I" + INCLUDE]
+HAND_WRITTEN = ["onee.cu", "linalg.cu", "scf.cu", "peaks.cu"]
+
+
+def nvcc_path():
+    env = os.environ.get("NVCC")
+    if env:
+        return env
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def _gen_module():
+    spec = importlib.util.spec_from_file_location("gen_eri", os.path.join(CSRC, "gen_eri.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _write(path, text):
+    if os.path.exists(path):
+        with open(path) as fh:
+            if fh.read() == text:
+                return
+    with open(path, "w") as fh:
+        fh.write(text)
+
+
+def generate_sources():
+    """Generated headers + per-class translation units + dispatch. Returns the
+    list of generated .cu files."""
+    g = _gen_module()
+    os.makedirs(GEN, exist_ok=True)
+    stats = g.generate(GEN)
+    heavy = {s[0]: s[6] for s in stats}
+    classes = g.classes()
+    names = [g.cls_name(c) for c in classes]
+    tus = []
+    for c, nm in zip(classes, names):
+        la, lb, lc, ld = c
+        same = (la, lb) == (lc, ld)
+        e = ['#include "eri_kernels.cuh"', '#include "internal.h"', f'#include "eri_{nm}.cuh"',
+             "namespace pimd {",
+             f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
+             "                     const double* D, double* G, const double* boys, double tau, cudaStream_t st)",
+             "{",
+             f"    if (ntiles > 0) jk_kernel<Cls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, G, boys, tau);",
+             "}"]
+        if same:
+            e += [f"void launch_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
+                  "                          const double* boys, double* Q, cudaStream_t st)",
+                  "{",
+                  f"    if (n > 0) schwarz_kernel<Cls_{nm}><<<(n + 127) / 128, 128, 0, st>>>(P, S, list, n, boys, Q);",
+                  "}"]
+        e.append("}  // namespace pimd\n")
+        p = os.path.join(GEN, f"tu_eri_{nm}.cu")
+        _write(p, "\n".join(e))
+        tus.append(p)
+        gl = ['#include "grad_kernels.cuh"', '#include "internal.h"', f'#include "grad_{nm}.cuh"']
+        if heavy[nm]:
+            gl.append(f'#include "grad_tape_{nm}.cuh"')
+        gl.append("namespace pimd {")
+        if not heavy[nm]:
+            gl += [f"void grad2e_upload_{nm}() {{}}",
+                   f"size_t grad2e_scratch_{nm}(int) {{ return 0; }}",
+                   f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
+                   "                        const double* D, double* grad, const double* boys, double tau, double*, int,",
+                   "                        cudaStream_t st)",
+                   "{",
+                   f"    if (ntiles > 0) grad2e_kernel<GCls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boys, tau);",
+                   "}"]
+        else:
+            gl += ["static TapeDev g_tape[64];",
+                   "static bool g_up[64];",
+                   "template <typename T> static const T* dev_copy(const T* h, size_t n)",
+                   "{",
+                   "    T* d = nullptr;",
+                   "    cudaMalloc(&d, n * sizeof(T));",
+                   "    cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice);",
+                   "    return d;",
+                   "}",
+                   f"void grad2e_upload_{nm}()",
+                   "{",
+                   "    int dev = 0;",
+                   "    cudaGetDevice(&dev);",
+                   "    if (dev < 0 || dev >= 64 || g_up[dev]) return;",
+                   "    TapeDev t;",
+                   "    t.vrr = dev_copy(tape_vrr, sizeof(tape_vrr) / sizeof(int));",
+                   "    t.acc = dev_copy(tape_acc, sizeof(tape_acc) / sizeof(int));",
+                   "    t.hrr = dev_copy(tape_hrr, sizeof(tape_hrr) / sizeof(int));",
+                   "    const int* outs[6] = {tape_outAp, tape_outBp, tape_outCp, tape_outAm, tape_outBm, tape_outCm};",
+                   "    const size_t nout[6] = {sizeof(tape_outAp), sizeof(tape_outBp), sizeof(tape_outCp),",
+                   "                            sizeof(tape_outAm), sizeof(tape_outBm), sizeof(tape_outCm)};",
+                   "    for (int k = 0; k < 6; k++) t.out[k] = dev_copy(outs[k], nout[k] / sizeof(int));",
+                   f"    t.nvrr = Tape_{nm}::NVRR;",
+                   f"    t.nacc = Tape_{nm}::NACC;",
+                   f"    t.nhrr = Tape_{nm}::NHRR;",
+                   f"    t.nslot = Tape_{nm}::NSLOT;",
+                   "    g_tape[dev] = t;",
+                   "    g_up[dev] = true;",
+                   "}",
+                   f"size_t grad2e_scratch_{nm}(int threads) {{ return (size_t)Tape_{nm}::NSLOT * threads * sizeof(double); }}",
+                   f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
+                   "                        const double* D, double* grad, const double* boys, double tau,",
+                   "                        double* scratch, int grid_blocks, cudaStream_t st)",
+                   "{",
+                   f"    grad2e_upload_{nm}();",
+                   "    int dev = 0;",
+                   "    cudaGetDevice(&dev);",
+                   f"    if (ntiles > 0) grad2e_tape_kernel<GCls_{nm}><<<grid_blocks, 128, 0, st>>>(P, S, R, tiles, ntiles, D,",
+                   "        grad, boys, tau, g_tape[dev], scratch);",
+                   "}"]
+        gl.append("}  // namespace pimd\n")
+        p = os.path.join(GEN, f"tu_grad_{nm}.cu")
+        _write(p, "\n".join(gl))
+        tus.append(p)
+    # dispatch
+    d = ['#include "internal.h"', "namespace pimd {"]
+    sig_jk = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
+              "double, cudaStream_t")
+    sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
+    sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
+             "double, double*, int, cudaStream_t")
+    for c, nm in zip(classes, names):
+        d.append(f"void launch_jk_{nm}({sig_jk});")
+        if (c[0], c[1]) == (c[2], c[3]):
+            d.append(f"void launch_schwarz_{nm}({sig_sw});")
+        d.append(f"void launch_grad2e_{nm}({sig_g});")
+        d.append(f"size_t grad2e_scratch_{nm}(int);")
+        d.append(f"void grad2e_upload_{nm}();")
+    d.append(f"int n_class_pairs() {{ return {len(classes)}; }}")
+    d.append("void class_pair_ls(int cp, int* la, int* lb, int* lc, int* ld)")
+    d.append("{")
+    d.append("    static const int t[][4] = {" + ", ".join("{%d, %d, %d, %d}" % c for c in classes) + "};")
+    d.append("    *la = t[cp][0]; *lb = t[cp][1]; *lc = t[cp][2]; *ld = t[cp][3];")
+    d.append("}")
+    flops = {s[0]: s[2] for s in stats}
+    d.append("long long class_vrr_flops(int cp)")
+    d.append("{")
+    d.append("    static const long long t[] = {" + ", ".join(str(flops[nm]) for nm in names) + "};")
+    d.append("    return t[cp];")
+    d.append("}")
+    d.append(f"typedef void (*JkFn)({sig_jk});")
+    d.append("static const JkFn jk_tab[] = {" + ", ".join(f"launch_jk_{nm}" for nm in names) + "};")
+    d.append("void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
+             "const double* D, double* G, const double* boys, double tau, cudaStream_t st)")
+    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, G, boys, tau, st); }")
+    same = [nm for c, nm in zip(classes, names) if (c[0], c[1]) == (c[2], c[3])]
+    d.append(f"typedef void (*SwFn)({sig_sw});")
+    d.append("static const SwFn sw_tab[] = {" + ", ".join(f"launch_schwarz_{nm}" for nm in same) + "};")
+    d.append("void launch_schwarz(int X, const Pairs& P, const Shells& S, const int* list, int n, const double* boys, "
+             "double* Q, cudaStream_t st)")
+    d.append("{ sw_tab[X](P, S, list, n, boys, Q, st); }")
+    d.append(f"typedef void (*GFn)({sig_g});")
+    d.append("static const GFn g_tab[] = {" + ", ".join(f"launch_grad2e_{nm}" for nm in names) + "};")
+    d.append("typedef size_t (*GsFn)(int);")
+    d.append("static const GsFn gs_tab[] = {" + ", ".join(f"grad2e_scratch_{nm}" for nm in names) + "};")
+    d.append("size_t grad2e_scratch_bytes(int cp, int threads) { return gs_tab[cp](threads); }")
+    d.append("void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
+             "const double* D, double* grad, const double* boys, double tau, double* scratch, int grid_blocks, "
+             "cudaStream_t st)")
+    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, tau, scratch, grid_blocks, st); }")
+    d.append("void grad2e_tapes_upload() {")
+    for nm in names:
+        d.append(f"    grad2e_upload_{nm}();")
+    d.append("}")
+    d.append("}  // namespace pimd\n")
+    p = os.path.join(GEN, "tu_dispatch.cu")
+    _write(p, "\n".join(d))
+    tus.append(p)
+    return tus
+
+
+def _deps_hash(src, extra):
+    h = hashlib.sha1()
+    h.update(" ".join(ARCH + FLAGS).encode())
+    with open(src, "rb") as fh:
+        h.update(fh.read())
+    for dep in extra:
+        with open(dep, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _compile(args):
+    src, obj, digest = args
+    stamp = obj + ".sha1"
+    if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == digest:
+        return src, 0.0, ""
+    import time
+    t = time.time()
+    cmd = [nvcc_path()] + ARCH + FLAGS + ["-c", src, "-o", obj + ".tmp"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    os.replace(obj + ".tmp", obj)
+    with open(stamp, "w") as fh:
+        fh.write(digest)
+    return src, time.time() - t, r.stderr
+
+
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    os.makedirs(OBJ, exist_ok=True)
+    tus = generate_sources()
+    common = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    common.append(os.path.join(INCLUDE, "pimdgb.h"))
+    work = []
+    for f in HAND_WRITTEN:
+        src = os.path.join(CSRC, f)
+        work.append((src, os.path.join(OBJ, f + ".o"), _deps_hash(src, common)))
+    for src in tus:
+        base = os.path.basename(src)
+        deps = list(common)
+        if base.startswith("tu_eri_") or base.startswith("tu_grad_"):
+            nm = base.split("_")[-1][:-3]
+            kind = "eri" if base.startswith("tu_eri_") else "grad"
+            deps.append(os.path.join(GEN, f"{kind}_{nm}.cuh"))
+            tp = os.path.join(GEN, f"grad_tape_{nm}.cuh")
+            if kind == "grad" and os.path.exists(tp):
+                deps.append(tp)
+        work.append((src, os.path.join(OBJ, base + ".o"), _deps_hash(src, deps)))
+    if force:
+        for _, obj, _ in work:
+            if os.path.exists(obj + ".sha1"):
+                os.remove(obj + ".sha1")
+    # largest units first so that the long ones start early
+    work.sort(key=lambda w: -os.path.getsize(w[0]) - sum(os.path.getsize(os.path.join(GEN, x))
+                                                            for x in os.listdir(GEN)
+                                                            if x.endswith(".cuh") and x[:-4].split("_")[-1]
+                                                            == os.path.basename(w[0])[:-3].split("_")[-1]))
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        for src, dt, err in ex.map(_compile, work):
+            if verbose and dt > 0:
+                print(f"  {os.path.basename(src)}: {dt:.1f}s", flush=True)
+    objs = [w[1] for w in work]
+    link_digest = hashlib.sha1("".join(open(o + ".sha1").read() for o in objs).encode()).hexdigest()
+    stamp = LIB + ".sha1"
+    if not (os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == link_digest):
+        cmd = [nvcc_path()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(LIB + ".tmp", LIB)
+        with open(stamp, "w") as fh:
+            fh.write(link_digest)
+    return LIB
+
+
+if __name__ == "__main__":
+    import time
+    t0 = time.time()
+    print(build(force="--force" in sys.argv, verbose=True), f"{time.time() - t0:.1f}s")

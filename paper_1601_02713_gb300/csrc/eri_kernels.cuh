@@ -1,0 +1,352 @@
+// Shell-quartet ERI kernels: Coulomb/exchange (Fock) build, Schwarz factors
+// and the two-electron part of the analytic RHF gradient.
+//
+// One thread evaluates one contracted shell quartet (ab|cd) of one replica:
+// the primitive loop runs the generated Obara-Saika vertical recursion into
+// contracted [e0|f0] accumulators, then the generated Head-Gordon-Pople
+// horizontal recursion gives the Cartesian block, which is turned into real
+// spherical d functions and contracted with the density on the fly.
+// A block of 128 threads shares one bra pair (staged in shared memory) and
+// walks 128 ket pairs of the same class, so the code path is uniform across
+// the block. Every replica of the call is covered by the same launch.
+//
+// Quartets are the canonical ones (a >= b, c >= d, ab >= cd); each is
+// scattered to its 8 permutations with weight f = 1/|stabiliser| into a
+// non-symmetric G' with F = h + G' + G'^T, where (per element)
+//   G'_ab += 2f D_cd v,  G'_cd += 2f D_ab v,
+//   G'_ac -= f/2 D_bd v, G'_bc -= f/2 D_ad v, G'_ad -= f/2 D_bc v, G'_bd -= f/2 D_ac v,
+// which reproduces F = h + J - K/2 with J_mn = sum D_ls (mn|ls) and
+// K_mn = sum D_ls (ml|ns) for a symmetric density.
+#pragma once
+#include "boys.cuh"
+#include "pimd_dev.cuh"
+
+namespace pimd {
+
+constexpr double kSqrt3 = 1.7320508075688772935;
+
+// in[N0][ncart(L)][N2] -> out[N0][nsph(L)][N2]; spherical d order m = -2..2:
+// sqrt3 xy, sqrt3 yz, zz - (xx + yy)/2, sqrt3 xz, sqrt3/2 (xx - yy)
+template <int N0, int L, int N2, typename T>
+__device__ __forceinline__ void sph_index(const T* __restrict__ in, T* __restrict__ out)
+{
+    if constexpr (L < 2) {
+#pragma unroll
+        for (int i = 0; i < N0 * ncart(L) * N2; i++) out[i] = in[i];
+    } else {
+#pragma unroll
+        for (int i0 = 0; i0 < N0; i0++)
+#pragma unroll
+            for (int i2 = 0; i2 < N2; i2++) {
+                const T* s = in + i0 * 6 * N2 + i2;
+                T* d = out + i0 * 5 * N2 + i2;
+                const T xx = s[0], xy = s[N2], xz = s[2 * N2], yy = s[3 * N2], yz = s[4 * N2], zz = s[5 * N2];
+                d[0] = T(kSqrt3) * xy;
+                d[N2] = T(kSqrt3) * yz;
+                d[2 * N2] = zz - T(0.5) * (xx + yy);
+                d[3 * N2] = T(kSqrt3) * xz;
+                d[4 * N2] = T(0.5 * kSqrt3) * (xx - yy);
+            }
+    }
+}
+
+// transpose of sph_index: in[N0][nsph(L)][N2] -> out[N0][ncart(L)][N2]
+template <int N0, int L, int N2, typename T>
+__device__ __forceinline__ void sph_index_t(const T* __restrict__ in, T* __restrict__ out)
+{
+    if constexpr (L < 2) {
+#pragma unroll
+        for (int i = 0; i < N0 * ncart(L) * N2; i++) out[i] = in[i];
+    } else {
+#pragma unroll
+        for (int i0 = 0; i0 < N0; i0++)
+#pragma unroll
+            for (int i2 = 0; i2 < N2; i2++) {
+                const T* s = in + i0 * 5 * N2 + i2;
+                T* d = out + i0 * 6 * N2 + i2;
+                const T m2 = s[0], m1 = s[N2], m0 = s[2 * N2], p1 = s[3 * N2], p2 = s[4 * N2];
+                d[0] = T(-0.5) * m0 + T(0.5 * kSqrt3) * p2;
+                d[N2] = T(kSqrt3) * m2;
+                d[2 * N2] = T(kSqrt3) * p1;
+                d[3 * N2] = T(-0.5) * m0 - T(0.5 * kSqrt3) * p2;
+                d[4 * N2] = T(kSqrt3) * m1;
+                d[5 * N2] = m0;
+            }
+    }
+}
+
+// Cartesian (ab|cd) block -> spherical block
+template <int LA, int LB, int LC, int LD, typename T>
+__device__ __forceinline__ void cart_to_sph4(T* __restrict__ buf, T* __restrict__ tmp)
+{
+    constexpr int ca = ncart(LA), cb = ncart(LB), cc = ncart(LC), cd = ncart(LD);
+    constexpr int sa = nsph(LA), sb = nsph(LB), sc = nsph(LC);
+    sph_index<1, LA, cb * cc * cd>(buf, tmp);
+    sph_index<sa, LB, cc * cd>(tmp, buf);
+    sph_index<sa * sb, LC, cd>(buf, tmp);
+    sph_index<sa * sb * sc, LD, 1>(tmp, buf);
+}
+
+template <int LA, int LB, int LC, int LD, typename T>
+__device__ __forceinline__ void sph_to_cart4_t(T* __restrict__ buf, T* __restrict__ tmp)
+{
+    constexpr int ca = ncart(LA), cb = ncart(LB), cc = ncart(LC);
+    constexpr int sb = nsph(LB), sc = nsph(LC), sd = nsph(LD);
+    sph_index_t<1, LA, sb * sc * sd>(buf, tmp);
+    sph_index_t<ca, LB, sc * sd>(tmp, buf);
+    sph_index_t<ca * cb, LC, sd>(buf, tmp);
+    sph_index_t<ca * cb * cc, LD, 1>(tmp, buf);
+}
+
+// Per-primitive-quartet quantities of the Obara-Saika recursion.
+struct PrimQuartet {
+    double PA[3], WP[3], QC[3], WQ[3];
+    double o2p, o2pr, o2q, o2qr, o2pq, T, theta;
+};
+
+__device__ __forceinline__ void prim_quartet(const double* bra, const double* ket, const double A[3],
+                                             const double C[3], PrimQuartet& g)
+{
+    // bra/ket: p, 1/p, Px, Py, Pz, K
+    const double p = bra[0], ip = bra[1], q = ket[0], iq = ket[1];
+    const double rs = rsqrt(p + q);
+    const double ipq = rs * rs;
+    const double rho = p * q * ipq;
+    double PQ2 = 0.0;
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        const double P = bra[2 + x], Q = ket[2 + x];
+        const double W = (p * P + q * Q) * ipq;
+        g.PA[x] = P - A[x];
+        g.WP[x] = W - P;
+        g.QC[x] = Q - C[x];
+        g.WQ[x] = W - Q;
+        PQ2 += (P - Q) * (P - Q);
+    }
+    g.T = rho * PQ2;
+    g.o2p = 0.5 * ip;
+    g.o2pr = g.o2p * rho * ip;
+    g.o2q = 0.5 * iq;
+    g.o2qr = g.o2q * rho * iq;
+    g.o2pq = 0.5 * ipq;
+    g.theta = bra[5] * ket[5] * rs;
+}
+
+__device__ __forceinline__ double atomic_add_d(double* a, double v) { return atomicAdd(a, v); }
+
+// Contract a spherical block with the density and scatter into G'.
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void scatter_jk(const double* __restrict__ I, double f, int fa, int fb, int fc, int fd,
+                                           int N, const double* __restrict__ D, double* __restrict__ G)
+{
+    constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
+    double Dab[na * nb], Dcd[nc * nd], Dac[na * nc], Dad[na * nd], Dbc[nb * nc], Dbd[nb * nd];
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nb; j++) Dab[i * nb + j] = __ldg(D + (size_t)(fa + i) * N + fb + j);
+#pragma unroll
+    for (int i = 0; i < nc; i++)
+#pragma unroll
+        for (int j = 0; j < nd; j++) Dcd[i * nd + j] = __ldg(D + (size_t)(fc + i) * N + fd + j);
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nc; j++) Dac[i * nc + j] = __ldg(D + (size_t)(fa + i) * N + fc + j);
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nd; j++) Dad[i * nd + j] = __ldg(D + (size_t)(fa + i) * N + fd + j);
+#pragma unroll
+    for (int i = 0; i < nb; i++)
+#pragma unroll
+        for (int j = 0; j < nc; j++) Dbc[i * nc + j] = __ldg(D + (size_t)(fb + i) * N + fc + j);
+#pragma unroll
+    for (int i = 0; i < nb; i++)
+#pragma unroll
+        for (int j = 0; j < nd; j++) Dbd[i * nd + j] = __ldg(D + (size_t)(fb + i) * N + fd + j);
+
+    // J'_ab and K'_ac, K'_ad (rows of the bra)
+#pragma unroll
+    for (int a = 0; a < na; a++) {
+#pragma unroll
+        for (int b = 0; b < nb; b++) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < nc; c++)
+#pragma unroll
+                for (int d = 0; d < nd; d++) s += Dcd[c * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
+            atomic_add_d(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * s);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < nc; c++)
+#pragma unroll
+        for (int d = 0; d < nd; d++) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < na; a++)
+#pragma unroll
+                for (int b = 0; b < nb; b++) s += Dab[a * nb + b] * I[((a * nb + b) * nc + c) * nd + d];
+            atomic_add_d(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * s);
+        }
+#pragma unroll
+    for (int a = 0; a < na; a++)
+#pragma unroll
+        for (int c = 0; c < nc; c++) {
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < nb; b++)
+#pragma unroll
+                for (int d = 0; d < nd; d++) s += Dbd[b * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
+            atomic_add_d(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * s);
+        }
+#pragma unroll
+    for (int b = 0; b < nb; b++)
+#pragma unroll
+        for (int c = 0; c < nc; c++) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < na; a++)
+#pragma unroll
+                for (int d = 0; d < nd; d++) s += Dad[a * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
+            atomic_add_d(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * s);
+        }
+#pragma unroll
+    for (int a = 0; a < na; a++)
+#pragma unroll
+        for (int d = 0; d < nd; d++) {
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < nb; b++)
+#pragma unroll
+                for (int c = 0; c < nc; c++) s += Dbc[b * nc + c] * I[((a * nb + b) * nc + c) * nd + d];
+            atomic_add_d(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * s);
+        }
+#pragma unroll
+    for (int b = 0; b < nb; b++)
+#pragma unroll
+        for (int d = 0; d < nd; d++) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < na; a++)
+#pragma unroll
+                for (int c = 0; c < nc; c++) s += Dac[a * nc + c] * I[((a * nb + b) * nc + c) * nd + d];
+            atomic_add_d(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * s);
+        }
+}
+
+// Load primitive pair data of pair g (fields P, IP, PX, PY, PZ, K) for prim k
+__device__ __forceinline__ void load_pp(const Pairs& P, int g, int k, double* out)
+{
+    const size_t n = P.n;
+#pragma unroll
+    for (int f = 0; f < 6; f++) out[f] = __ldg(P.pp + ((size_t)f * PIMD_MAXPP + k) * n + g);
+}
+
+// contracted Cartesian block of one quartet via the generated recursion
+template <class C>
+__device__ __forceinline__ void quartet_cart(const double (*sbra)[PIMD_MAXPP], int nbra, const Pairs& P, int cd,
+                                             const double A[3], const double B[3], const double Cc[3],
+                                             const double Dd[3], const double* __restrict__ boys, double* cart)
+{
+    double acc[C::NE * C::NF];
+#pragma unroll
+    for (int i = 0; i < C::NE * C::NF; i++) acc[i] = 0.0;
+    const int nket = P.npp[cd];
+    for (int j = 0; j < nket; j++) {
+        double ket[6];
+        load_pp(P, cd, j, ket);
+        for (int i = 0; i < nbra; i++) {
+            double bra[6];
+#pragma unroll
+            for (int f = 0; f < 6; f++) bra[f] = sbra[f][i];
+            PrimQuartet g;
+            prim_quartet(bra, ket, A, Cc, g);
+            double F[C::L + 1];
+            boys_eval<C::L>(g.T, boys, F);
+#pragma unroll
+            for (int m = 0; m <= C::L; m++) F[m] *= g.theta;
+            C::template vrr<double>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1], g.QC[2], g.WQ[0],
+                g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, acc);
+        }
+    }
+    C::template hrr<double>(acc, A[0] - B[0], A[1] - B[1], A[2] - B[2], Cc[0] - Dd[0], Cc[1] - Dd[1], Cc[2] - Dd[2], cart);
+}
+
+// Fock (G') build over the quartets of one class pair. blockDim.x == 128.
+template <class C>
+__global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
+                                                 const double* __restrict__ Dall, double* __restrict__ Gall,
+                                                 const double* __restrict__ boys, double tau)
+{
+    __shared__ double sbra[6][PIMD_MAXPP];
+    const Tile t = tiles[blockIdx.x];
+    if (!R.active[t.rep]) return;
+    const int ab = t.ab;
+    if (threadIdx.x < 6 * PIMD_MAXPP) {
+        const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
+        sbra[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
+    }
+    __syncthreads();
+    const int cd = t.c0 + threadIdx.x;
+    if (cd >= t.c1) return;
+    const double Qab = P.Q[ab], Qcd = P.Q[cd];
+    if (Qab * Qcd < tau) return;
+    const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
+    double A[3], B[3], Cc[3], Dd[3];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        A[x] = S.xyz[3 * sa + x];
+        B[x] = S.xyz[3 * sb + x];
+        Cc[x] = S.xyz[3 * sc + x];
+        Dd[x] = S.xyz[3 * sd + x];
+    }
+    constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
+    double cart[NCART], tmp[NCART];
+    quartet_cart<C>(sbra, P.npp[ab], P, cd, A, B, Cc, Dd, boys, cart);
+    cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
+    double f = 1.0;
+    if (sa == sb) f *= 0.5;
+    if (sc == sd) f *= 0.5;
+    if (ab == cd) f *= 0.5;
+    const int r = t.rep;
+    const int N = R.nbf[r];
+    const size_t off = R.moff[r];
+    scatter_jk<C::LA, C::LB, C::LC, C::LD>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
+                                           Gall + off);
+}
+
+// Schwarz factors: Q_ab = sqrt(max over functions of (mn|mn)), one thread per pair
+template <class C>
+__global__ void __launch_bounds__(128) schwarz_kernel(Pairs P, Shells S, const int* __restrict__ list, int n,
+                                                      const double* __restrict__ boys, double* __restrict__ Qout)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int ab = list[idx];
+    const int sa = P.sa[ab], sb = P.sb[ab];
+    double sbra_l[6][PIMD_MAXPP];
+    const int np = P.npp[ab];
+    for (int k = 0; k < np; k++)
+        for (int f = 0; f < 6; f++) sbra_l[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
+    double A[3], B[3];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        A[x] = S.xyz[3 * sa + x];
+        B[x] = S.xyz[3 * sb + x];
+    }
+    constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
+    double cart[NCART], tmp[NCART];
+    quartet_cart<C>(sbra_l, np, P, ab, A, B, A, B, boys, cart);
+    cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
+    constexpr int na = nsph(C::LA), nb = nsph(C::LB);
+    double m = 0.0;
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nb; j++) m = fmax(m, fabs(cart[((i * nb + j) * na + i) * nb + j]));
+    Qout[ab] = sqrt(m);
+}
+
+}  // namespace pimd

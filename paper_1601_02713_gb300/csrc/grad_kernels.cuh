@@ -1,0 +1,350 @@
+// Two-electron part of the analytic RHF gradient from derivative ERIs.
+//
+//   g_X += sum_{mnls} [ 1/2 D_mn D_ls - 1/4 D_ml D_ns ] d(mn|ls)/dX
+//
+// summed over canonical quartets with weight f = 1/|stabiliser|; the bracket
+// summed over the 8 index permutations is Gamma = 4 D_ab D_cd - D_ac D_bd -
+// D_ad D_bc. Derivatives of a Cartesian Gaussian with respect to its centre,
+//   d/dA_i g_a = 2 alpha g_{a+1_i} - a_i g_{a-1_i},
+// are taken for centres A, B and C from one shared Obara-Saika recursion whose
+// primitives are accumulated four times (unweighted and weighted by 2 alpha,
+// 2 beta, 2 gamma); centre D follows from translational invariance,
+// dD = -(dA + dB + dC). Gamma is built in the spherical basis and taken back to
+// Cartesian components with the transpose of the spherical transform.
+#pragma once
+#include "eri_kernels.cuh"
+
+namespace pimd {
+
+// Cartesian exponents of component idx of a shell of angular momentum l
+__device__ __forceinline__ void cart_of(int l, int idx, int& lx, int& ly, int& lz)
+{
+    int n = 0;
+    for (int x = l; x >= 0; x--)
+        for (int y = l - x; y >= 0; y--) {
+            if (n == idx) {
+                lx = x;
+                ly = y;
+                lz = l - x - y;
+                return;
+            }
+            n++;
+        }
+    lx = ly = lz = 0;
+}
+
+__device__ __forceinline__ int cidx(int lx, int ly, int lz)
+{
+    const int l = lx + ly + lz;
+    return (l - lx) * (l - lx + 1) / 2 + lz;
+}
+
+// Gamma of one quartet in Cartesian components: Gc[((a*nb+b)*nc+c)*nd+d]
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void gamma_cart(double f, int fa, int fb, int fc, int fd, int N,
+                                           const double* __restrict__ D, double* Gc, double* tmp)
+{
+    constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
+    for (int a = 0; a < na; a++)
+        for (int b = 0; b < nb; b++) {
+            const double dab = __ldg(D + (size_t)(fa + a) * N + fb + b);
+            for (int c = 0; c < nc; c++) {
+                const double dac = __ldg(D + (size_t)(fa + a) * N + fc + c);
+                const double dbc = __ldg(D + (size_t)(fb + b) * N + fc + c);
+                for (int d = 0; d < nd; d++) {
+                    const double dcd = __ldg(D + (size_t)(fc + c) * N + fd + d);
+                    const double dbd = __ldg(D + (size_t)(fb + b) * N + fd + d);
+                    const double dad = __ldg(D + (size_t)(fa + a) * N + fd + d);
+                    Gc[((a * nb + b) * nc + c) * nd + d] = f * (4.0 * dab * dcd - dac * dbd - dad * dbc);
+                }
+            }
+        }
+    sph_to_cart4_t<LA, LB, LC, LD>(Gc, tmp);
+}
+
+// sum_{abcd} Gc * d(ab|cd)/dX_i for X at position POS (0: A, 1: B, 2: C), given
+// accessors for the raised (l+1) and lowered (l-1) blocks of that position.
+template <int LA, int LB, int LC, int LD, int POS, class Up, class Dn>
+__device__ __forceinline__ void contract_deriv(const double* Gc, Up up, Dn dn, double g[3])
+{
+    constexpr int L[4] = {LA, LB, LC, LD};
+    constexpr int n[4] = {ncart(LA), ncart(LB), ncart(LC), ncart(LD)};
+    int nu[4] = {n[0], n[1], n[2], n[3]};
+    int ndn[4] = {n[0], n[1], n[2], n[3]};
+    nu[POS] = ncart(L[POS] + 1);
+    ndn[POS] = L[POS] > 0 ? ncart(L[POS] - 1) : 1;
+    g[0] = g[1] = g[2] = 0.0;
+    for (int i0 = 0; i0 < n[0]; i0++)
+        for (int i1 = 0; i1 < n[1]; i1++)
+            for (int i2 = 0; i2 < n[2]; i2++)
+                for (int i3 = 0; i3 < n[3]; i3++) {
+                    const double gm = Gc[((i0 * n[1] + i1) * n[2] + i2) * n[3] + i3];
+                    int idx[4] = {i0, i1, i2, i3};
+                    int e[3];
+                    cart_of(L[POS], idx[POS], e[0], e[1], e[2]);
+#pragma unroll
+                    for (int x = 0; x < 3; x++) {
+                        int eu[3] = {e[0], e[1], e[2]};
+                        eu[x]++;
+                        int ju[4] = {i0, i1, i2, i3};
+                        ju[POS] = cidx(eu[0], eu[1], eu[2]);
+                        double v = up(((ju[0] * nu[1] + ju[1]) * nu[2] + ju[2]) * nu[3] + ju[3]);
+                        if (e[x] > 0) {
+                            int ed[3] = {e[0], e[1], e[2]};
+                            ed[x]--;
+                            int jd[4] = {i0, i1, i2, i3};
+                            jd[POS] = cidx(ed[0], ed[1], ed[2]);
+                            v -= e[x] * dn(((jd[0] * ndn[1] + jd[1]) * ndn[2] + jd[2]) * ndn[3] + jd[3]);
+                        }
+                        g[x] += gm * v;
+                    }
+                }
+}
+
+struct ArrAcc {
+    const double* p;
+    __device__ __forceinline__ double operator()(int i) const { return p[i]; }
+};
+
+// load the 8 primitive-pair fields (P, IP, PX, PY, PZ, K, EA, EB)
+__device__ __forceinline__ void load_pp8(const Pairs& P, int g, int k, double* out)
+{
+    const size_t n = P.n;
+#pragma unroll
+    for (int f = 0; f < 8; f++) out[f] = __ldg(P.pp + ((size_t)f * PIMD_MAXPP + k) * n + g);
+}
+
+__device__ __forceinline__ void scatter_grad(double* grad, const Shells& S, int sa, int sb, int sc, int sd,
+                                             const double gA[3], const double gB[3], const double gC[3])
+{
+    const int aa = S.atom[sa], ab = S.atom[sb], ac = S.atom[sc], ad = S.atom[sd];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        atomicAdd(grad + 3 * aa + x, gA[x]);
+        atomicAdd(grad + 3 * ab + x, gB[x]);
+        atomicAdd(grad + 3 * ac + x, gC[x]);
+        atomicAdd(grad + 3 * ad + x, -(gA[x] + gB[x] + gC[x]));
+    }
+}
+
+// Straight-line gradient kernel (generated VRR/HRR), blockDim.x == 128.
+template <class G>
+__global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
+                                                     const double* __restrict__ Dall, double* __restrict__ grad,
+                                                     const double* __restrict__ boys, double tau)
+{
+    constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
+    __shared__ double sbra[8][PIMD_MAXPP];
+    const Tile t = tiles[blockIdx.x];
+    const int ab = t.ab;
+    if (threadIdx.x < 8 * PIMD_MAXPP) {
+        const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
+        sbra[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
+    }
+    __syncthreads();
+    const int cd = t.c0 + threadIdx.x;
+    if (cd >= t.c1) return;
+    if (P.Q[ab] * P.Q[cd] < tau) return;
+    const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
+    double A[3], B[3], Cc[3], Dd[3];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        A[x] = S.xyz[3 * sa + x];
+        B[x] = S.xyz[3 * sb + x];
+        Cc[x] = S.xyz[3 * sc + x];
+        Dd[x] = S.xyz[3 * sd + x];
+    }
+    double accU[G::N_accU], accA[G::N_accA], accB[G::N_accB], accC[G::N_accC];
+    for (int i = 0; i < G::N_accU; i++) accU[i] = 0.0;
+    for (int i = 0; i < G::N_accA; i++) accA[i] = 0.0;
+    for (int i = 0; i < G::N_accB; i++) accB[i] = 0.0;
+    for (int i = 0; i < G::N_accC; i++) accC[i] = 0.0;
+    const int nbra = P.npp[ab], nket = P.npp[cd];
+    for (int j = 0; j < nket; j++) {
+        double ket[8];
+        load_pp8(P, cd, j, ket);
+        for (int i = 0; i < nbra; i++) {
+            double bra[6];
+#pragma unroll
+            for (int f = 0; f < 6; f++) bra[f] = sbra[f][i];
+            PrimQuartet g;
+            prim_quartet(bra, ket, A, Cc, g);
+            double F[G::L + 1];
+            boys_eval<G::L>(g.T, boys, F);
+#pragma unroll
+            for (int m = 0; m <= G::L; m++) F[m] *= g.theta;
+            G::template vrr<double>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1],
+                                    g.QC[2], g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, accU,
+                                    accA, accB, accC, 2.0 * sbra[6][i], 2.0 * sbra[7][i], 2.0 * ket[6]);
+        }
+    }
+    const double AB0 = A[0] - B[0], AB1 = A[1] - B[1], AB2 = A[2] - B[2];
+    const double CD0 = Cc[0] - Dd[0], CD1 = Cc[1] - Dd[1], CD2 = Cc[2] - Dd[2];
+    constexpr int NC = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
+    double Gc[NC], tmp[NC];
+    double f = 1.0;
+    if (sa == sb) f *= 0.5;
+    if (sc == sd) f *= 0.5;
+    if (ab == cd) f *= 0.5;
+    const int r = t.rep;
+    gamma_cart<LA, LB, LC, LD>(f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], R.nbf[r], Dall + R.moff[r], Gc, tmp);
+    double gA[3], gB[3], gC[3];
+    {
+        double up[ncart(LA + 1) * ncart(LB) * ncart(LC) * ncart(LD)];
+        G::template hrrAp<double>(accA, AB0, AB1, AB2, CD0, CD1, CD2, up);
+        if constexpr (LA > 0) {
+            double dn[ncart(LA > 0 ? LA - 1 : 0) * ncart(LB) * ncart(LC) * ncart(LD)];
+            G::template hrrAm<double>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
+            contract_deriv<LA, LB, LC, LD, 0>(Gc, ArrAcc{up}, ArrAcc{dn}, gA);
+        } else {
+            contract_deriv<LA, LB, LC, LD, 0>(Gc, ArrAcc{up}, ArrAcc{up}, gA);
+        }
+    }
+    {
+        double up[ncart(LA) * ncart(LB + 1) * ncart(LC) * ncart(LD)];
+        G::template hrrBp<double>(accB, AB0, AB1, AB2, CD0, CD1, CD2, up);
+        if constexpr (LB > 0) {
+            double dn[ncart(LA) * ncart(LB > 0 ? LB - 1 : 0) * ncart(LC) * ncart(LD)];
+            G::template hrrBm<double>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
+            contract_deriv<LA, LB, LC, LD, 1>(Gc, ArrAcc{up}, ArrAcc{dn}, gB);
+        } else {
+            contract_deriv<LA, LB, LC, LD, 1>(Gc, ArrAcc{up}, ArrAcc{up}, gB);
+        }
+    }
+    {
+        double up[ncart(LA) * ncart(LB) * ncart(LC + 1) * ncart(LD)];
+        G::template hrrCp<double>(accC, AB0, AB1, AB2, CD0, CD1, CD2, up);
+        if constexpr (LC > 0) {
+            double dn[ncart(LA) * ncart(LB) * ncart(LC > 0 ? LC - 1 : 0) * ncart(LD)];
+            G::template hrrCm<double>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
+            contract_deriv<LA, LB, LC, LD, 2>(Gc, ArrAcc{up}, ArrAcc{dn}, gC);
+        } else {
+            contract_deriv<LA, LB, LC, LD, 2>(Gc, ArrAcc{up}, ArrAcc{up}, gC);
+        }
+    }
+    scatter_grad(grad, S, sa, sb, sc, sd, gA, gB, gC);
+}
+
+// ---------------------------------------------------------------------------
+// Tape interpreter for the gradient classes whose straight-line code would be
+// too large: the same recursions, read as op lists, with every intermediate in
+// a per-thread slice of a global scratch buffer laid out [slot][thread] so that
+// a warp's accesses coalesce. Persistent grid; blockDim.x == 128.
+// ---------------------------------------------------------------------------
+struct TapeDev {
+    const int* vrr;   // 8 ints per op
+    const int* acc;
+    const int* hrr;
+    const int* out[6];  // Ap, Bp, Cp, Am, Bm, Cm output slots
+    int nvrr, nacc, nhrr, nslot;
+};
+
+struct ScrAcc {
+    const double* s;
+    const int* slot;
+    size_t stride;
+    __device__ __forceinline__ double operator()(int i) const { return s[(size_t)__ldg(slot + i) * stride]; }
+};
+
+template <class G>
+__global__ void __launch_bounds__(128) grad2e_tape_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
+                                                          int ntiles, const double* __restrict__ Dall,
+                                                          double* __restrict__ grad, const double* __restrict__ boys,
+                                                          double tau, TapeDev tp, double* __restrict__ scratch)
+{
+    constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
+    __shared__ double sbra[8][PIMD_MAXPP];
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    double* Sx = scratch + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const Tile t = tiles[tile];
+        const int ab = t.ab;
+        __syncthreads();
+        if (threadIdx.x < 8 * PIMD_MAXPP) {
+            const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
+            sbra[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
+        }
+        __syncthreads();
+        const int cd = t.c0 + threadIdx.x;
+        if (cd >= t.c1) continue;
+        if (P.Q[ab] * P.Q[cd] < tau) continue;
+        const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
+        double A[3], B[3], Cc[3], Dd[3];
+#pragma unroll
+        for (int x = 0; x < 3; x++) {
+            A[x] = S.xyz[3 * sa + x];
+            B[x] = S.xyz[3 * sb + x];
+            Cc[x] = S.xyz[3 * sc + x];
+            Dd[x] = S.xyz[3 * sd + x];
+        }
+        for (int o = 0; o < tp.nacc; o++) Sx[(size_t)__ldg(tp.acc + 8 * o + 1) * stride] = 0.0;
+        const int nbra = P.npp[ab], nket = P.npp[cd];
+        for (int j = 0; j < nket; j++) {
+            double ket[8];
+            load_pp8(P, cd, j, ket);
+            for (int i = 0; i < nbra; i++) {
+                double bra[6];
+#pragma unroll
+                for (int f = 0; f < 6; f++) bra[f] = sbra[f][i];
+                PrimQuartet g;
+                prim_quartet(bra, ket, A, Cc, g);
+                double F[G::L + 1];
+                boys_eval<G::L>(g.T, boys, F);
+#pragma unroll
+                for (int m = 0; m <= G::L; m++) Sx[(size_t)m * stride] = F[m] * g.theta;
+                for (int o = 0; o < tp.nvrr; o++) {
+                    const int* op = tp.vrr + 8 * o;
+                    const int kind = __ldg(op), dst = __ldg(op + 1), s1 = __ldg(op + 2), s2 = __ldg(op + 3);
+                    const int s3 = __ldg(op + 4), s4 = __ldg(op + 5), s5 = __ldg(op + 6), aux = __ldg(op + 7);
+                    const int dir = aux & 15, k1 = (aux >> 4) & 15, k2 = aux >> 8;
+                    double v;
+                    if (kind == 0) {
+                        const double pa = dir == 0 ? g.PA[0] : (dir == 1 ? g.PA[1] : g.PA[2]);
+                        const double wp = dir == 0 ? g.WP[0] : (dir == 1 ? g.WP[1] : g.WP[2]);
+                        v = pa * Sx[(size_t)s1 * stride] + wp * Sx[(size_t)s2 * stride];
+                        if (s3 >= 0) v += k1 * (g.o2p * Sx[(size_t)s3 * stride] - g.o2pr * Sx[(size_t)s4 * stride]);
+                    } else {
+                        const double qc = dir == 0 ? g.QC[0] : (dir == 1 ? g.QC[1] : g.QC[2]);
+                        const double wq = dir == 0 ? g.WQ[0] : (dir == 1 ? g.WQ[1] : g.WQ[2]);
+                        v = qc * Sx[(size_t)s1 * stride] + wq * Sx[(size_t)s2 * stride];
+                        if (s3 >= 0) v += k1 * (g.o2q * Sx[(size_t)s3 * stride] - g.o2qr * Sx[(size_t)s4 * stride]);
+                        if (s5 >= 0) v += k2 * g.o2pq * Sx[(size_t)s5 * stride];
+                    }
+                    Sx[(size_t)dst * stride] = v;
+                }
+                const double w[4] = {1.0, 2.0 * sbra[6][i], 2.0 * sbra[7][i], 2.0 * ket[6]};
+                for (int o = 0; o < tp.nacc; o++) {
+                    const int* op = tp.acc + 8 * o;
+                    const int dst = __ldg(op + 1), src = __ldg(op + 2), ws = __ldg(op + 7);
+                    const double wv = ws == 0 ? w[0] : (ws == 1 ? w[1] : (ws == 2 ? w[2] : w[3]));
+                    Sx[(size_t)dst * stride] += wv * Sx[(size_t)src * stride];
+                }
+            }
+        }
+        const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+        const double CD[3] = {Cc[0] - Dd[0], Cc[1] - Dd[1], Cc[2] - Dd[2]};
+        for (int o = 0; o < tp.nhrr; o++) {
+            const int* op = tp.hrr + 8 * o;
+            const int kind = __ldg(op), dst = __ldg(op + 1), s1 = __ldg(op + 2), s2 = __ldg(op + 3);
+            const int dir = __ldg(op + 7);
+            const double c = kind == 3 ? (dir == 0 ? AB[0] : (dir == 1 ? AB[1] : AB[2]))
+                                       : (dir == 0 ? CD[0] : (dir == 1 ? CD[1] : CD[2]));
+            Sx[(size_t)dst * stride] = Sx[(size_t)s1 * stride] + c * Sx[(size_t)s2 * stride];
+        }
+        constexpr int NC = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
+        double Gc[NC], tmp[NC];
+        double f = 1.0;
+        if (sa == sb) f *= 0.5;
+        if (sc == sd) f *= 0.5;
+        if (ab == cd) f *= 0.5;
+        const int r = t.rep;
+        gamma_cart<LA, LB, LC, LD>(f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], R.nbf[r], Dall + R.moff[r], Gc, tmp);
+        double gA[3], gB[3], gC[3];
+        contract_deriv<LA, LB, LC, LD, 0>(Gc, ScrAcc{Sx, tp.out[0], stride}, ScrAcc{Sx, tp.out[3], stride}, gA);
+        contract_deriv<LA, LB, LC, LD, 1>(Gc, ScrAcc{Sx, tp.out[1], stride}, ScrAcc{Sx, tp.out[4], stride}, gB);
+        contract_deriv<LA, LB, LC, LD, 2>(Gc, ScrAcc{Sx, tp.out[2], stride}, ScrAcc{Sx, tp.out[5], stride}, gC);
+        scatter_grad(grad, S, sa, sb, sc, sd, gA, gB, gC);
+    }
+}
+
+}  // namespace pimd

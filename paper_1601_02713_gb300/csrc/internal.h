@@ -1,0 +1,107 @@
+// Internal interface between the host-side SCF driver and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pimd_dev.cuh"
+
+namespace pimd {
+
+// molecule-level arrays of one call (all replicas concatenated)
+struct AtomsDev {
+    const double* xyz;      // [natom_total][3]
+    const double* Z;        // [natom_total]
+    const int* rep_atom0;   // [nrep + 1] first atom of each replica
+};
+
+struct BasisPrimDev {
+    const double* exps;     // normalised basis primitives
+    const double* coefs;
+    const int* sprim;       // per shell: first primitive in exps/coefs
+    const int* snprim;      // per shell: number of primitives
+};
+
+// pair data of `npair` pairs listed in P (sa/sb already set)
+void launch_pair_data(const Pairs& P, int* npp, double* pp, const Shells& S, const BasisPrimDev& B,
+                      cudaStream_t st);
+
+// S, T, V (spherical) of every pair into the replica matrices
+void launch_one_electron(const Pairs& P, const Shells& S, const BasisPrimDev& B, const AtomsDev& At,
+                         const Reps& R, double* Sm, double* Tm, double* Vm, const double* boys, cudaStream_t st);
+
+// one-electron gradient: 2 sum D dh/dA - 2 sum W dS/dA (bra derivatives over ordered pairs)
+// plus the Hellmann-Feynman term, accumulated into grad[natom_total][3]
+void launch_grad_1e(const Pairs& P, const Shells& S, const BasisPrimDev& B, const AtomsDev& At, const Reps& R,
+                    const double* D, const double* W, double* grad, const double* boys, cudaStream_t st);
+
+// nuclear repulsion energy per replica (added into enn[rep]) and its gradient
+void launch_vnn(const AtomsDev& At, int natom_total, const int* atom_rep, double* enn, double* grad,
+                cudaStream_t st);
+
+// ERI kernels, per class pair index (0..20 over (X, Y), X >= Y in the order
+// ss, ps, pp, ds, dp, dd)
+int n_class_pairs();
+void class_pair_ls(int cp, int* la, int* lb, int* lc, int* ld);
+long long class_vrr_flops(int cp);
+void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
+               const double* D, double* G, const double* boys, double tau, cudaStream_t st);
+void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n, const double* boys,
+                    double* Q, cudaStream_t st);
+// gradient: returns scratch bytes the tape path needs for class pair cp (0 if straight-line)
+size_t grad2e_scratch_bytes(int cp, int grid_threads);
+void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
+                   const double* D, double* grad, const double* boys, double tau, double* scratch,
+                   int grid_blocks, cudaStream_t st);
+void grad2e_tapes_upload();   // once per device
+void boys_table_upload(double** dev_tab);
+
+// ------------------------------------------------------------------ linalg
+struct GemmDesc {
+    int M, N, K;
+    const double* A;
+    int lda, ta;
+    const double* B;
+    int ldb, tb;
+    double* C;
+    int ldc;
+    double alpha, beta;
+    int rep;          // replica (checked against the active mask; -1: always)
+};
+void launch_gemm(const GemmDesc* d_desc, int ndesc, int maxM, int maxN, const int* active, cudaStream_t st);
+
+struct RepMat {       // per replica matrix view
+    int N, nocc;
+    long long off;    // element offset of the N x N matrices
+};
+// one-sided Jacobi eigensolver of symmetric A (per replica, ascending order):
+// evals[rep][N] (offset rep * ldE), V columns = eigenvectors (row-major N x N at off)
+void launch_jacobi(const RepMat* d_rm, int nrep, const double* A, double* V, double* evals, int ldE,
+                   double* work, const int* active, int shift_to_spd, cudaStream_t st);
+
+void launch_fock_assemble(const RepMat* rm, int nrep, const double* h, const double* G, double* F,
+                          const int* active, cudaStream_t st);
+void launch_energy(const RepMat* rm, int nrep, const double* D, const double* h, const double* F,
+                   const double* enn, double* E, const int* active, cudaStream_t st);
+void launch_antisym(const RepMat* rm, int nrep, const double* M, double* E, const int* active, cudaStream_t st);
+void launch_maxabs(const RepMat* rm, int nrep, const double* A, double* out, const int* active, cudaStream_t st);
+void launch_orth_from_eig(const RepMat* rm, int nrep, const double* U, const double* s, int ldE, double* X,
+                          cudaStream_t st);
+void launch_scale_cols(const RepMat* rm, int nrep, const double* C, const double* evals, int ldE, double* out,
+                       const int* mask, cudaStream_t st);
+// DIIS
+void launch_diis_store(const RepMat* rm, int nrep, const double* F, const double* E, double* Fh, double* Eh,
+                       const int* slot, int hist, const int* active, cudaStream_t st);
+void launch_diis_dots(const RepMat* rm, int nrep, const double* Eh, const int* slot, const int* count, int hist,
+                      double* B, const int* active, cudaStream_t st);
+void launch_diis_solve(int nrep, const double* B, const int* slot, const int* count, int hist, double* coef,
+                       const int* active, cudaStream_t st);
+void launch_diis_combine(const RepMat* rm, int nrep, const double* Fh, const double* coef, int hist,
+                         const double* F, double* Fbar, const int* diis_on, const int* active, cudaStream_t st);
+void launch_copy_mats(const RepMat* rm, int nrep, const double* src, double* dst, const int* mask,
+                      cudaStream_t st);
+void launch_boys_eval(int n, int m, const double* T, double* F, const double* boys, cudaStream_t st);
+void gather_xyz(const double* atom_xyz, const int* shell_atom, int nshell, double* shell_xyz, cudaStream_t st);
+void add_mats(const RepMat* rm, int nrep, const double* A, const double* B, double* C, cudaStream_t st);
+void diis_set_stride(long long stride);
+
+}  // namespace pimd

@@ -1,0 +1,64 @@
+// Device-side data layout shared by the kernels of the batched RHF library.
+//
+// Every replica (PIMD bead or string image) of one call is laid out
+// side by side: shells, shell pairs and matrices of all replicas live in
+// single arrays, indexed by global shell / pair ids and by per-replica matrix
+// offsets, so that one launch covers the whole batch (the paper's n replicas
+// of a step, Sec. 2), ragged sizes included.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PIMD_MAXPRIM 3                       // primitives per contracted shell
+#define PIMD_MAXPP (PIMD_MAXPRIM * PIMD_MAXPRIM)
+#define PIMD_LMAX 2                          // s, p, d shells
+
+namespace pimd {
+
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ constexpr int nsph(int l) { return l < 2 ? ncart(l) : 2 * l + 1; }
+// position of (lx, ly, lz) in the order lx = l..0, ly = l-lx..0
+__host__ __device__ constexpr int cart_index(int lx, int ly, int lz)
+{
+    return (lx + ly + lz - lx) * (lx + ly + lz - lx + 1) / 2 + lz;
+}
+
+// primitive-pair fields, stored SoA: pp[((f * PIMD_MAXPP) + k) * npair + g]
+enum PPField {
+    PP_P = 0,   // p = a + b
+    PP_IP,      // 1 / p
+    PP_PX, PP_PY, PP_PZ,  // Gaussian product centre P
+    PP_K,       // sqrt(2) pi^{5/4} c_a c_b exp(-ab/p |AB|^2) / p
+    PP_EA, PP_EB,         // exponents a, b (gradient weights)
+    PP_NF
+};
+
+struct Shells {           // all replicas concatenated
+    const double* xyz;    // [nshell][3] centre (bohr)
+    const int* l;
+    const int* bf;        // first basis function within the replica
+    const int* atom;      // global atom index
+    const int* rep;       // replica index
+};
+
+struct Pairs {
+    int n;                // number of shell pairs (all replicas)
+    const int* sa;        // shell with the larger l
+    const int* sb;
+    const int* npp;       // primitive pairs kept
+    const double* pp;     // SoA primitive-pair data
+    const double* Q;      // Schwarz factor sqrt(max |(ab|ab)|)
+};
+
+struct Reps {
+    const int* nbf;             // functions per replica
+    const long long* moff;      // offset of the replica's N x N matrices
+    const int* active;          // 1 while the replica's SCF runs
+};
+
+// one block of quartets: bra pair ab with ket pairs [c0, c1)
+struct Tile {
+    int ab, c0, c1, rep;
+};
+
+}  // namespace pimd

@@ -1,0 +1,1067 @@
+// Host-side driver and C ABI of the batched RHF library.
+//
+// One call evaluates every replica of a step (the paper's n replicas, Sec. 2)
+// with the same sequence of batched launches:
+//   shells/pairs bookkeeping -> primitive-pair data -> Schwarz factors ->
+//   sorted pair lists and quartet tiles (cutoff 1e-12, Sec. 3.1) ->
+//   S, T, V, h, V_nn -> X = S^{-1/2} -> guess (core Hamiltonian, or the
+//   replica's MOs from the previous call, Sec. 2) -> SCF iterations
+//   (Fock build, energy, DIIS error, DIIS, diagonalisation, density) with a
+//   per-replica convergence mask -> W, one- and two-electron gradient, V_nn.
+// Replicas that converge leave the batch while the others keep iterating, so
+// the launch never waits on a finished replica (the load imbalance of
+// Sec. 3.2 is absorbed inside the batch).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/pimdgb.h"
+#include "boys.cuh"
+#include "internal.h"
+
+using namespace pimd;
+
+// ---------------------------------------------------------------------------
+// basis
+// ---------------------------------------------------------------------------
+struct ShellDef {
+    int l, nprim;
+    double exps[PIMD_MAXPRIM];
+    double coefs[PIMD_MAXPRIM];  // normalised (x^l component)
+};
+
+struct pimd_basis {
+    std::map<int, int> elem;               // Z -> element index
+    std::vector<std::vector<ShellDef>> shells;
+    std::vector<int> nbf_elem;
+    // flattened primitives (element-major, shell order) for the device
+    std::vector<double> exps, coefs;
+    std::vector<std::vector<int>> prim_off;  // per element, per shell
+};
+
+static double dfact(int n)
+{
+    double r = 1.0;
+    for (int k = n; k > 1; k -= 2) r *= k;
+    return r;
+}
+
+// normalised contraction: primitive norm (2a/pi)^{3/4} (4a)^{l/2} / sqrt((2l-1)!!),
+// then the contraction scaled so that <phi|phi> = 1 for the x^l component,
+// <g_a|g_b> = (pi/(a+b))^{3/2} (2l-1)!! / (2(a+b))^l
+static void normalise(ShellDef& s)
+{
+    const double pi = 3.14159265358979323846;
+    double c[PIMD_MAXPRIM];
+    for (int i = 0; i < s.nprim; i++) {
+        const double a = s.exps[i];
+        c[i] = s.coefs[i] * pow(2 * a / pi, 0.75) * pow(4 * a, 0.5 * s.l) / sqrt(dfact(2 * s.l - 1));
+    }
+    double ov = 0.0;
+    for (int i = 0; i < s.nprim; i++)
+        for (int j = 0; j < s.nprim; j++) {
+            const double p = s.exps[i] + s.exps[j];
+            ov += c[i] * c[j] * pow(pi / p, 1.5) * dfact(2 * s.l - 1) / pow(2 * p, s.l);
+        }
+    for (int i = 0; i < s.nprim; i++) s.coefs[i] = c[i] / sqrt(ov);
+}
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct pimd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    double* boys = nullptr;
+    std::map<std::string, DevBuf> bufs;
+    std::string last_error;
+    pimd_stats stats{};
+    // MO cache keyed by replica index
+    struct MO {
+        std::vector<int> Z;
+        int N = 0;
+        DevBuf C;
+    };
+    std::vector<MO> mo;
+    cudaEvent_t ev[8];
+    int nsm = 152;
+};
+
+static int set_err(pimd_ctx* ctx, int code, const std::string& msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return set_err(ctx, PIMD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+static int dev_ensure(pimd_ctx* ctx, const char* name, size_t count, T** out)
+{
+    DevBuf& b = ctx->bufs[name];
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (b.cap < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, PIMD_ENOMEM, std::string("cudaMalloc failed for ") + name);
+        }
+        b.cap = bytes;
+    }
+    *out = (T*)b.p;
+    return PIMD_OK;
+}
+
+#define ENSURE(name, count, ptr)                                   \
+    do {                                                           \
+        int rc_ = dev_ensure(ctx, name, (size_t)(count), &(ptr)); \
+        if (rc_) return rc_;                                       \
+    } while (0)
+
+template <typename T>
+static int upload(pimd_ctx* ctx, const char* name, const std::vector<T>& v, T** out)
+{
+    int rc = dev_ensure(ctx, name, v.size(), out);
+    if (rc) return rc;
+    if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return PIMD_OK;
+}
+
+#define UPLOAD(name, vec, ptr)                      \
+    do {                                            \
+        int rc_ = upload(ctx, name, vec, &(ptr));   \
+        if (rc_) return rc_;                        \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// C ABI: options, context, basis
+// ---------------------------------------------------------------------------
+extern "C" void pimd_scf_opts_default(pimd_scf_opts* o)
+{
+    memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(*o);
+    o->conv_energy = 1e-10;
+    o->conv_error = 1e-8;
+    o->max_iter = 64;
+    o->diis_size = 8;
+    o->schwarz_tau = 1e-12;
+    o->fp32_tau = 0.0;
+    o->guess = 0;
+    o->deterministic = 0;
+    o->want_gradient = 1;
+}
+
+extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
+{
+    if (!out) return PIMD_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return PIMD_ECUDA;
+    }
+    pimd_ctx* ctx = new pimd_ctx();
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return PIMD_ECUDA;
+    }
+    boys_table_upload(&ctx->boys);
+    grad2e_tapes_upload();
+    for (int i = 0; i < 8; i++) cudaEventCreate(&ctx->ev[i]);
+    cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
+    if (cudaGetLastError() != cudaSuccess) {
+        delete ctx;
+        return PIMD_ECUDA;
+    }
+    *out = ctx;
+    return PIMD_OK;
+}
+
+extern "C" void pimd_ctx_destroy(pimd_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->bufs)
+        if (kv.second.p) cudaFree(kv.second.p);
+    for (auto& m : ctx->mo)
+        if (m.C.p) cudaFree(m.C.p);
+    if (ctx->boys) cudaFree(ctx->boys);
+    for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" void pimd_ctx_clear_guess(pimd_ctx* ctx)
+{
+    if (!ctx) return;
+    for (auto& m : ctx->mo) {
+        m.Z.clear();
+        m.N = 0;
+    }
+}
+
+extern "C" int pimd_basis_create(pimd_basis** out, int nelem, const int* Z_of_elem, const int* nshell_of_elem,
+                                 const int* shell_l, const int* shell_nprim, const double* exps,
+                                 const double* coefs, int spherical)
+{
+    if (!out || nelem <= 0 || !Z_of_elem || !nshell_of_elem || !shell_l || !shell_nprim || !exps || !coefs)
+        return PIMD_EINVAL;
+    if (spherical != 1) return PIMD_EINVAL;
+    pimd_basis* b = new pimd_basis();
+    int s = 0, p = 0;
+    for (int e = 0; e < nelem; e++) {
+        const int Z = Z_of_elem[e];
+        if (Z < 1 || Z > 118 || b->elem.count(Z) || nshell_of_elem[e] <= 0) {
+            delete b;
+            return PIMD_EINVAL;
+        }
+        b->elem[Z] = e;
+        std::vector<ShellDef> sh;
+        std::vector<int> offs;
+        int nbf = 0;
+        for (int k = 0; k < nshell_of_elem[e]; k++, s++) {
+            ShellDef d;
+            d.l = shell_l[s];
+            d.nprim = shell_nprim[s];
+            if (d.l < 0 || d.l > PIMD_LMAX || d.nprim < 1 || d.nprim > PIMD_MAXPRIM) {
+                delete b;
+                return PIMD_EINVAL;
+            }
+            for (int i = 0; i < d.nprim; i++, p++) {
+                d.exps[i] = exps[p];
+                d.coefs[i] = coefs[p];
+                if (!(exps[p] > 0.0) || !isfinite(exps[p]) || !isfinite(coefs[p])) {
+                    delete b;
+                    return PIMD_EINVAL;
+                }
+            }
+            normalise(d);
+            offs.push_back((int)b->exps.size());
+            for (int i = 0; i < d.nprim; i++) {
+                b->exps.push_back(d.exps[i]);
+                b->coefs.push_back(d.coefs[i]);
+            }
+            nbf += nsph(d.l);
+            sh.push_back(d);
+        }
+        b->shells.push_back(sh);
+        b->prim_off.push_back(offs);
+        b->nbf_elem.push_back(nbf);
+    }
+    *out = b;
+    return PIMD_OK;
+}
+
+extern "C" void pimd_basis_destroy(pimd_basis* b) { delete b; }
+
+extern "C" int pimd_basis_nbf(const pimd_basis* b, int natom, const int* Z)
+{
+    if (!b || natom < 0 || (natom > 0 && !Z)) return PIMD_EINVAL;
+    int n = 0;
+    for (int i = 0; i < natom; i++) {
+        auto it = b->elem.find(Z[i]);
+        if (it == b->elem.end()) return PIMD_EINVAL;
+        n += b->nbf_elem[it->second];
+    }
+    return n;
+}
+
+extern "C" const char* pimd_strerror(int code)
+{
+    switch (code) {
+        case PIMD_OK: return "ok";
+        case PIMD_EINVAL: return "invalid argument";
+        case PIMD_ENOMEM: return "device allocation failed";
+        case PIMD_ECUDA: return "CUDA runtime error";
+        case PIMD_ENOTCONV: return "SCF did not converge for some replica";
+        case PIMD_ETIMEOUT: return "bounded device wait expired";
+        case PIMD_EBASIS: return "overlap matrix numerically singular";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out)
+{
+    if (!ctx || !out) return PIMD_EINVAL;
+    *out = ctx->stats;
+    return PIMD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch setup
+// ---------------------------------------------------------------------------
+struct Batch {
+    int nrep = 0;
+    std::vector<int> natom, atom0, nbf, nocc;
+    std::vector<long long> moff;
+    long long mtot = 0;
+    int maxN = 0;
+    // shells
+    std::vector<int> sh_l, sh_bf, sh_atom, sh_rep, sh_prim, sh_nprim;
+    std::vector<int> rep_sh0;
+    // pairs grouped by (rep, class)
+    std::vector<int> pa, pb;
+    std::vector<int> grp0;   // [nrep * 6 + 1] start of group (rep, X)
+    // tiles per class pair
+    std::vector<std::vector<Tile>> tiles;
+    std::vector<long long> nq_cp;
+    long long nquart = 0;
+    std::vector<long long> nquart_rep;
+    double vrr_flops = 0.0;
+    // device views
+    Pairs P{};
+    Shells S{};
+    Reps R{};
+    AtomsDev At{};
+    BasisPrimDev B{};
+    std::vector<Tile*> d_tiles;
+};
+
+static int pair_class(int la, int lb)
+{
+    // order ss, ps, pp, ds, dp, dd
+    static const int t[3][3] = {{0, -1, -1}, {1, 2, -1}, {3, 4, 5}};
+    return t[la][lb];
+}
+
+static int class_pair_index(int X, int Y)
+{
+    return X * (X + 1) / 2 + Y;  // X >= Y, same order as the generator
+}
+
+// validate and lay out replicas; coordinates already on the device (d_xyz)
+static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, const int* Zc, const double* d_xyz,
+                       const pimd_basis* basis, double tau)
+{
+    bt.nrep = nrep;
+    bt.natom.assign(natom_of, natom_of + nrep);
+    bt.atom0.resize(nrep + 1);
+    bt.nbf.resize(nrep);
+    bt.nocc.resize(nrep);
+    bt.moff.resize(nrep + 1);
+    bt.rep_sh0.resize(nrep + 1);
+    int a0 = 0;
+    long long moff = 0;
+    std::vector<double> Zd;
+    std::vector<int> atom_rep;
+    for (int r = 0; r < nrep; r++) {
+        bt.atom0[r] = a0;
+        bt.rep_sh0[r] = (int)bt.sh_l.size();
+        int nel = 0, nbf = 0;
+        for (int i = 0; i < natom_of[r]; i++) {
+            const int Z = Zc[a0 + i];
+            auto it = basis->elem.find(Z);
+            if (it == basis->elem.end()) return set_err(ctx, PIMD_EINVAL, "element missing from basis");
+            nel += Z;
+            const int e = it->second;
+            for (size_t k = 0; k < basis->shells[e].size(); k++) {
+                const ShellDef& d = basis->shells[e][k];
+                bt.sh_l.push_back(d.l);
+                bt.sh_bf.push_back(nbf);
+                bt.sh_atom.push_back(a0 + i);
+                bt.sh_rep.push_back(r);
+                bt.sh_prim.push_back(basis->prim_off[e][k]);
+                bt.sh_nprim.push_back(d.nprim);
+                nbf += nsph(d.l);
+            }
+            Zd.push_back((double)Z);
+            atom_rep.push_back(r);
+        }
+        if (nel % 2) return set_err(ctx, PIMD_EINVAL, "odd electron count (RHF needs a closed shell)");
+        bt.nbf[r] = nbf;
+        bt.nocc[r] = nel / 2;
+        if (bt.nocc[r] > nbf) return set_err(ctx, PIMD_EINVAL, "more occupied orbitals than basis functions");
+        bt.moff[r] = moff;
+        moff += (long long)nbf * nbf;
+        bt.maxN = std::max(bt.maxN, nbf);
+        a0 += natom_of[r];
+    }
+    bt.atom0[nrep] = a0;
+    bt.rep_sh0[nrep] = (int)bt.sh_l.size();
+    bt.moff[nrep] = moff;
+    bt.mtot = moff;
+    const int nsh = (int)bt.sh_l.size();
+
+    // pairs grouped by (rep, class)
+    std::vector<std::vector<std::pair<int, int>>> groups((size_t)nrep * 6);
+    for (int r = 0; r < nrep; r++)
+        for (int a = bt.rep_sh0[r]; a < bt.rep_sh0[r + 1]; a++)
+            for (int b = bt.rep_sh0[r]; b <= a; b++) {
+                int x = a, y = b;
+                if (bt.sh_l[y] > bt.sh_l[x]) std::swap(x, y);
+                groups[(size_t)r * 6 + pair_class(bt.sh_l[x], bt.sh_l[y])].push_back({x, y});
+            }
+    bt.grp0.assign((size_t)nrep * 6 + 1, 0);
+    bt.pa.clear();
+    bt.pb.clear();
+    for (size_t g = 0; g < groups.size(); g++) {
+        bt.grp0[g] = (int)bt.pa.size();
+        for (auto& pr : groups[g]) {
+            bt.pa.push_back(pr.first);
+            bt.pb.push_back(pr.second);
+        }
+    }
+    bt.grp0[groups.size()] = (int)bt.pa.size();
+    const int npair = (int)bt.pa.size();
+
+    // device: atoms, shells
+    double* d_Z;
+    int *d_atom0, *d_atom_rep;
+    UPLOAD("Z", Zd, d_Z);
+    UPLOAD("atom0", bt.atom0, d_atom0);
+    UPLOAD("atom_rep", atom_rep, d_atom_rep);
+    bt.At.xyz = d_xyz;
+    bt.At.Z = d_Z;
+    bt.At.rep_atom0 = d_atom0;
+    int *d_l, *d_bf, *d_satom, *d_srep, *d_sprim, *d_snprim;
+    UPLOAD("sh_l", bt.sh_l, d_l);
+    UPLOAD("sh_bf", bt.sh_bf, d_bf);
+    UPLOAD("sh_atom", bt.sh_atom, d_satom);
+    UPLOAD("sh_rep", bt.sh_rep, d_srep);
+    UPLOAD("sh_prim", bt.sh_prim, d_sprim);
+    UPLOAD("sh_nprim", bt.sh_nprim, d_snprim);
+    double* d_exps;
+    double* d_coefs;
+    UPLOAD("b_exps", basis->exps, d_exps);
+    UPLOAD("b_coefs", basis->coefs, d_coefs);
+    bt.B = BasisPrimDev{d_exps, d_coefs, d_sprim, d_snprim};
+    // shell centres gathered from the atom coordinates on the device
+    double* d_shxyz;
+    ENSURE("sh_xyz", (size_t)nsh * 3, d_shxyz);
+    {
+        std::vector<int> src(bt.sh_atom);
+        int* d_src;
+        UPLOAD("sh_src", src, d_src);
+        gather_xyz(d_xyz, d_src, nsh, d_shxyz, ctx->stream);
+    }
+    bt.S = Shells{d_shxyz, d_l, d_bf, d_satom, d_srep};
+
+    // replicas
+    int* d_nbf;
+    long long* d_moff;
+    UPLOAD("nbf", bt.nbf, d_nbf);
+    UPLOAD("moff", bt.moff, d_moff);
+    int* d_active;
+    ENSURE("active", nrep, d_active);
+    bt.R = Reps{d_nbf, d_moff, d_active};
+
+    // pair data, Schwarz factors (unsorted), then sort each group by Q
+    int *d_pa, *d_pb, *d_npp;
+    double *d_pp, *d_Q;
+    UPLOAD("pa", bt.pa, d_pa);
+    UPLOAD("pb", bt.pb, d_pb);
+    ENSURE("npp", npair, d_npp);
+    ENSURE("pp", (size_t)PP_NF * PIMD_MAXPP * npair, d_pp);
+    ENSURE("Q", npair, d_Q);
+    bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q};
+    launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
+    ctx->stats.kernel_launches += 2;
+    for (int X = 0; X < 6; X++) {
+        std::vector<int> list;
+        for (int r = 0; r < nrep; r++)
+            for (int g = bt.grp0[r * 6 + X]; g < bt.grp0[r * 6 + X + 1]; g++) list.push_back(g);
+        if (list.empty()) continue;
+        int* d_list;
+        std::string nm = "sw_list" + std::to_string(X);
+        UPLOAD(nm.c_str(), list, d_list);
+        launch_schwarz(X, bt.P, bt.S, d_list, (int)list.size(), ctx->boys, d_Q, ctx->stream);
+        ctx->stats.kernel_launches++;
+    }
+    CK(cudaGetLastError());
+    std::vector<double> Q(npair);
+    if (npair) CK(cudaMemcpyAsync(Q.data(), d_Q, sizeof(double) * npair, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q < npair; q++)
+        if (!isfinite(Q[q])) return set_err(ctx, PIMD_EINVAL, "non-finite integrals (check coordinates)");
+    {
+        std::vector<int> perm(npair);
+        for (int i = 0; i < npair; i++) perm[i] = i;
+        for (size_t g = 0; g + 1 < bt.grp0.size(); g++)
+            std::stable_sort(perm.begin() + bt.grp0[g], perm.begin() + bt.grp0[g + 1],
+                             [&](int x, int y) { return Q[x] > Q[y]; });
+        std::vector<int> pa2(npair), pb2(npair);
+        std::vector<double> Q2(npair);
+        for (int i = 0; i < npair; i++) {
+            pa2[i] = bt.pa[perm[i]];
+            pb2[i] = bt.pb[perm[i]];
+            Q2[i] = Q[perm[i]];
+        }
+        bt.pa.swap(pa2);
+        bt.pb.swap(pb2);
+        Q.swap(Q2);
+        UPLOAD("pa", bt.pa, d_pa);
+        UPLOAD("pb", bt.pb, d_pb);
+        UPLOAD("Q", Q, d_Q);
+        bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q};
+        launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
+    }
+    // quartet tiles: for bra pair i of class X and ket class Y <= X, the ket
+    // pairs with Q_j >= tau / Q_i form a prefix of the sorted group.
+    const int ncp = n_class_pairs();
+    bt.tiles.assign(ncp, {});
+    bt.nq_cp.assign(ncp, 0);
+    bt.nquart = 0;
+    bt.nquart_rep.assign(nrep, 0);
+    bt.vrr_flops = 0.0;
+    for (int X = 0; X < 6; X++)
+        for (int Y = 0; Y <= X; Y++) {
+            const int cp = class_pair_index(X, Y);
+            auto& tl = bt.tiles[cp];
+            for (int r = 0; r < nrep; r++) {
+                const int b0 = bt.grp0[r * 6 + X], b1 = bt.grp0[r * 6 + X + 1];
+                const int k0 = bt.grp0[r * 6 + Y], k1 = bt.grp0[r * 6 + Y + 1];
+                for (int i = b0; i < b1; i++) {
+                    if (Q[i] <= 0.0) continue;
+                    const double thr = tau / Q[i];
+                    // first index in [k0, k1) with Q < thr (Q descending)
+                    int lo = k0, hi = k1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) / 2;
+                        if (Q[mid] >= thr) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    int kend = lo;
+                    if (X == Y) kend = std::min(kend, i + 1);
+                    if (kend <= k0) continue;
+                    const long long nqi = kend - k0;
+                    bt.nq_cp[cp] += nqi;
+                    bt.nquart_rep[r] += nqi;
+                    const double npp_i = (double)bt.sh_nprim[bt.pa[i]] * bt.sh_nprim[bt.pb[i]];
+                    double npp_k = 0.0;
+                    for (int k = k0; k < kend; k++) npp_k += (double)bt.sh_nprim[bt.pa[k]] * bt.sh_nprim[bt.pb[k]];
+                    bt.vrr_flops += npp_i * npp_k * (double)class_vrr_flops(cp);
+                    for (int c = k0; c < kend; c += 128) tl.push_back(Tile{i, c, std::min(c + 128, kend), r});
+                }
+            }
+            bt.nquart += bt.nq_cp[cp];
+        }
+    bt.d_tiles.assign(ncp, nullptr);
+    for (int cp = 0; cp < ncp; cp++) {
+        if (bt.tiles[cp].empty()) continue;
+        std::string nm = "tiles" + std::to_string(cp);
+        UPLOAD(nm.c_str(), bt.tiles[cp], bt.d_tiles[cp]);
+    }
+    CK(cudaGetLastError());
+    return PIMD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SCF
+// ---------------------------------------------------------------------------
+struct Mats {
+    double *S, *H, *T, *V, *X, *F, *G, *D, *Fb, *M1, *M2, *Er, *C, *Cp, *W, *Ev, *work, *Cs;
+    double *Fh, *Eh, *Bd, *coef;
+    double *E, *emax, *enn;
+    int *slot, *count, *diis_on, *active, *fin;
+    RepMat* rm;
+    int ldE;
+};
+
+static int alloc_mats(pimd_ctx* ctx, Batch& bt, Mats& m, int hist)
+{
+    const long long mt = bt.mtot;
+    ENSURE("S", mt, m.S);
+    ENSURE("H", mt, m.H);
+    ENSURE("T", mt, m.T);
+    ENSURE("V", mt, m.V);
+    ENSURE("X", mt, m.X);
+    ENSURE("F", mt, m.F);
+    ENSURE("G", mt, m.G);
+    ENSURE("D", mt, m.D);
+    ENSURE("Fb", mt, m.Fb);
+    ENSURE("M1", mt, m.M1);
+    ENSURE("M2", mt, m.M2);
+    ENSURE("Er", mt, m.Er);
+    ENSURE("C", mt, m.C);
+    ENSURE("Cp", mt, m.Cp);
+    ENSURE("W", mt, m.W);
+    ENSURE("work", mt, m.work);
+    ENSURE("Cs", mt, m.Cs);
+    m.ldE = bt.maxN;
+    ENSURE("Ev", (size_t)bt.nrep * m.ldE, m.Ev);
+    const long long stride = (long long)bt.maxN * bt.maxN;
+    ENSURE("Fh", (size_t)bt.nrep * hist * stride, m.Fh);
+    ENSURE("Eh", (size_t)bt.nrep * hist * stride, m.Eh);
+    ENSURE("Bd", (size_t)bt.nrep * hist * hist, m.Bd);
+    ENSURE("coef", (size_t)bt.nrep * hist, m.coef);
+    ENSURE("E", bt.nrep, m.E);
+    ENSURE("emax", bt.nrep, m.emax);
+    ENSURE("enn", bt.nrep, m.enn);
+    ENSURE("slot", bt.nrep, m.slot);
+    ENSURE("count", bt.nrep, m.count);
+    ENSURE("diis_on", bt.nrep, m.diis_on);
+    ENSURE("fin", bt.nrep, m.fin);
+    m.active = (int*)bt.R.active;
+    std::vector<RepMat> rm(bt.nrep);
+    for (int r = 0; r < bt.nrep; r++) rm[r] = RepMat{bt.nbf[r], bt.nocc[r], bt.moff[r]};
+    UPLOAD("rm", rm, m.rm);
+    diis_set_stride(stride);
+    return PIMD_OK;
+}
+
+struct GemmSet {
+    GemmDesc* d = nullptr;
+    int n = 0, maxM = 0, maxN = 0;
+};
+
+// per-replica GEMM descriptors: C = alpha op(A) op(B) + beta C, square N x N
+// unless K is the occupied count
+static int make_gemm(pimd_ctx* ctx, const char* name, const Batch& bt, const double* A, int ta, const double* B,
+                     int tb, double* C, double alpha, bool kocc, GemmSet& gs)
+{
+    std::vector<GemmDesc> v(bt.nrep);
+    for (int r = 0; r < bt.nrep; r++) {
+        const int N = bt.nbf[r];
+        const long long o = bt.moff[r];
+        v[r] = GemmDesc{N, N, kocc ? bt.nocc[r] : N, A + o, N, ta, B + o, N, tb, C + o, N, alpha, 0.0, r};
+    }
+    UPLOAD(name, v, gs.d);
+    gs.n = bt.nrep;
+    gs.maxM = gs.maxN = bt.maxN;
+    return PIMD_OK;
+}
+
+struct ScfPlan {
+    GemmSet FD, FDS, XtE, XtEX, XtF, XtFX, XC, Dn, Wn;
+};
+
+static int make_plan(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p)
+{
+    int rc;
+    if ((rc = make_gemm(ctx, "g_FD", bt, m.F, 0, m.D, 0, m.M1, 1.0, false, p.FD))) return rc;
+    if ((rc = make_gemm(ctx, "g_FDS", bt, m.M1, 0, m.S, 0, m.M2, 1.0, false, p.FDS))) return rc;
+    if ((rc = make_gemm(ctx, "g_XtE", bt, m.X, 1, m.Er, 0, m.M1, 1.0, false, p.XtE))) return rc;
+    if ((rc = make_gemm(ctx, "g_XtEX", bt, m.M1, 0, m.X, 0, m.M2, 1.0, false, p.XtEX))) return rc;
+    if ((rc = make_gemm(ctx, "g_XtF", bt, m.X, 1, m.Fb, 0, m.M1, 1.0, false, p.XtF))) return rc;
+    if ((rc = make_gemm(ctx, "g_XtFX", bt, m.M1, 0, m.X, 0, m.Cs, 1.0, false, p.XtFX))) return rc;
+    if ((rc = make_gemm(ctx, "g_XC", bt, m.X, 0, m.Cp, 0, m.C, 1.0, false, p.XC))) return rc;
+    if ((rc = make_gemm(ctx, "g_Dn", bt, m.C, 0, m.C, 1, m.D, 2.0, true, p.Dn))) return rc;
+    if ((rc = make_gemm(ctx, "g_Wn", bt, m.Cs, 0, m.C, 1, m.W, 2.0, true, p.Wn))) return rc;
+    return PIMD_OK;
+}
+
+static void gemm(pimd_ctx* ctx, const GemmSet& g, const int* mask)
+{
+    launch_gemm(g.d, g.n, g.maxM, g.maxN, mask, ctx->stream);
+    ctx->stats.kernel_launches++;
+}
+
+// Fbar -> X^T Fbar X -> eigen -> C = X C', D = 2 C_occ C_occ^T (replicas in mask)
+static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, const int* mask)
+{
+    gemm(ctx, p.XtF, mask);
+    gemm(ctx, p.XtFX, mask);   // -> Cs (scratch)
+    launch_jacobi(m.rm, bt.nrep, m.Cs, m.Cp, m.Ev, m.ldE, m.work, mask, 1, ctx->stream);
+    gemm(ctx, p.XC, mask);
+    gemm(ctx, p.Dn, mask);
+    ctx->stats.kernel_launches++;
+}
+
+static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau)
+{
+    CK(cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream));
+    for (int cp = 0; cp < n_class_pairs(); cp++) {
+        if (bt.tiles[cp].empty()) continue;
+        launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, m.G, ctx->boys, tau,
+                  ctx->stream);
+        ctx->stats.kernel_launches++;
+    }
+    return PIMD_OK;
+}
+
+static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc, const double* d_xyz,
+                     const pimd_basis* basis, const pimd_scf_opts* o, double* d_E, double* d_grad, pimd_info* info)
+{
+    Batch bt;
+    ctx->stats = pimd_stats{};
+    CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+    int rc = setup_batch(ctx, bt, nrep, natom_of, Zc, d_xyz, basis, o->schwarz_tau);
+    if (rc) return rc;
+    const int hist = std::max(2, std::min(8, o->diis_size));
+    Mats m;
+    if ((rc = alloc_mats(ctx, bt, m, hist))) return rc;
+    ScfPlan plan;
+    if ((rc = make_plan(ctx, bt, m, plan))) return rc;
+    std::vector<int> active(nrep, 1), fin(nrep, 0), slot(nrep, hist - 1), count(nrep, 0), diis_on(nrep, 0);
+    UPLOAD("active", active, m.active);
+    bt.R.active = m.active;
+    // one-electron part
+    launch_one_electron(bt.P, bt.S, bt.B, bt.At, bt.R, m.S, m.T, m.V, ctx->boys, ctx->stream);
+    {
+        add_mats(m.rm, nrep, m.T, m.V, m.H, ctx->stream);
+    }
+    CK(cudaMemsetAsync(m.enn, 0, sizeof(double) * nrep, ctx->stream));
+    {
+        std::vector<int> atom_rep;
+        for (int r = 0; r < nrep; r++)
+            for (int i = 0; i < bt.natom[r]; i++) atom_rep.push_back(r);
+        int* d_ar;
+        UPLOAD("atom_rep2", atom_rep, d_ar);
+        launch_vnn(bt.At, bt.atom0[nrep], d_ar, m.enn, nullptr, ctx->stream);
+    }
+    // X = S^{-1/2}
+    launch_jacobi(m.rm, nrep, m.S, m.Cp, m.Ev, m.ldE, m.work, nullptr, 0, ctx->stream);
+    ctx->stats.kernel_launches += 5;
+    {
+        std::vector<double> ev((size_t)nrep * m.ldE);
+        CK(cudaMemcpyAsync(ev.data(), m.Ev, sizeof(double) * ev.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int r = 0; r < nrep; r++)
+            if (bt.nbf[r] > 0 && ev[(size_t)r * m.ldE] < 1e-8)
+                return set_err(ctx, PIMD_EBASIS, "overlap matrix numerically singular");
+    }
+    launch_orth_from_eig(m.rm, nrep, m.Cp, m.Ev, m.ldE, m.X, ctx->stream);
+    // guess: cached MOs of the same replica index, else the core Hamiltonian
+    if ((int)ctx->mo.size() < nrep) ctx->mo.resize(nrep);
+    std::vector<int> use_cache(nrep, 0), core(nrep, 0);
+    for (int r = 0; r < nrep; r++) {
+        auto& mo = ctx->mo[r];
+        std::vector<int> z(Zc + bt.atom0[r], Zc + bt.atom0[r + 1]);
+        use_cache[r] = (o->guess == 1 && mo.N == bt.nbf[r] && mo.Z == z);
+        core[r] = !use_cache[r];
+        if (use_cache[r])
+            CK(cudaMemcpyAsync(m.C + bt.moff[r], mo.C.p, sizeof(double) * bt.nbf[r] * bt.nbf[r],
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    int* d_mask;
+    UPLOAD("mask_core", core, d_mask);
+    launch_copy_mats(m.rm, nrep, m.H, m.Fb, d_mask, ctx->stream);
+    diag_density(ctx, bt, m, plan, d_mask);
+    {
+        int* d_mc;
+        UPLOAD("mask_cache", use_cache, d_mc);
+        gemm(ctx, plan.Dn, d_mc);
+    }
+    // SCF iterations
+    std::vector<double> E(nrep), emax(nrep), Eprev(nrep, 0.0);
+    std::vector<int> iters(nrep, 0), conv(nrep, 0);
+    std::vector<double> fdE(nrep, 0.0), ferr(nrep, 0.0);
+    int nactive = nrep;
+    for (int it = 1; it <= o->max_iter && nactive > 0; it++) {
+        CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+        if ((rc = fock_build(ctx, bt, m, o->schwarz_tau))) return rc;
+        CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+        ctx->stats.fock_builds++;
+        launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, m.active, ctx->stream);
+        launch_energy(m.rm, nrep, m.D, m.H, m.F, m.enn, m.E, m.active, ctx->stream);
+        gemm(ctx, plan.FD, m.active);
+        gemm(ctx, plan.FDS, m.active);
+        launch_antisym(m.rm, nrep, m.M2, m.Er, m.active, ctx->stream);
+        gemm(ctx, plan.XtE, m.active);
+        gemm(ctx, plan.XtEX, m.active);   // error -> M2
+        launch_maxabs(m.rm, nrep, m.M2, m.emax, m.active, ctx->stream);
+        ctx->stats.kernel_launches += 4;
+        CK(cudaMemcpyAsync(E.data(), m.E, sizeof(double) * nrep, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(emax.data(), m.emax, sizeof(double) * nrep, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaGetLastError());
+        {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+            ctx->stats.ms_fock += ms;
+        }
+        bool anyfin = false;
+        for (int r = 0; r < nrep; r++) {
+            fin[r] = 0;
+            if (!active[r]) continue;
+            if (!isfinite(E[r])) return set_err(ctx, PIMD_ECUDA, "non-finite SCF energy");
+            iters[r] = it;
+            fdE[r] = it > 1 ? fabs(E[r] - Eprev[r]) : INFINITY;
+            ferr[r] = emax[r];
+            if (it > 1 && fdE[r] < o->conv_energy && emax[r] < o->conv_error) {
+                fin[r] = 1;
+                conv[r] = 1;
+                anyfin = true;
+            } else if (it == o->max_iter) {
+                fin[r] = 1;
+                anyfin = true;
+            }
+            Eprev[r] = E[r];
+        }
+        if (anyfin) {
+            // finishing replicas: orbitals, D and W from F(D) itself
+            UPLOAD("fin", fin, m.fin);
+            launch_copy_mats(m.rm, nrep, m.F, m.Fb, m.fin, ctx->stream);
+            diag_density(ctx, bt, m, plan, m.fin);
+            launch_scale_cols(m.rm, nrep, m.C, m.Ev, m.ldE, m.Cs, m.fin, ctx->stream);
+            gemm(ctx, plan.Wn, m.fin);
+            ctx->stats.kernel_launches += 2;
+            for (int r = 0; r < nrep; r++)
+                if (fin[r]) {
+                    active[r] = 0;
+                    nactive--;
+                }
+            UPLOAD("active", active, m.active);
+        }
+        if (nactive == 0) break;
+        // DIIS on the continuing replicas
+        for (int r = 0; r < nrep; r++)
+            if (active[r]) {
+                slot[r] = (slot[r] + 1) % hist;
+                count[r] = std::min(count[r] + 1, hist);
+                diis_on[r] = count[r] >= 2;
+            }
+        int *d_slot, *d_count, *d_on;
+        UPLOAD("slot", slot, d_slot);
+        UPLOAD("count", count, d_count);
+        UPLOAD("diis_on", diis_on, d_on);
+        launch_diis_store(m.rm, nrep, m.F, m.M2, m.Fh, m.Eh, d_slot, hist, m.active, ctx->stream);
+        launch_diis_dots(m.rm, nrep, m.Eh, d_slot, d_count, hist, m.Bd, m.active, ctx->stream);
+        launch_diis_solve(nrep, m.Bd, d_slot, d_count, hist, m.coef, m.active, ctx->stream);
+        launch_diis_combine(m.rm, nrep, m.Fh, m.coef, hist, m.F, m.Fb, d_on, m.active, ctx->stream);
+        ctx->stats.kernel_launches += 4;
+        diag_density(ctx, bt, m, plan, m.active);
+    }
+    CK(cudaGetLastError());
+    // energies
+    CK(cudaMemcpyAsync(d_E, E.data(), sizeof(double) * nrep, cudaMemcpyHostToDevice, ctx->stream));
+    // gradient
+    if (o->want_gradient && d_grad) {
+        const int natot = bt.atom0[nrep];
+        CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * natot * 3, ctx->stream));
+        launch_grad_1e(bt.P, bt.S, bt.B, bt.At, bt.R, m.D, m.W, d_grad, ctx->boys, ctx->stream);
+        {
+            int* d_ar = (int*)ctx->bufs["atom_rep2"].p;
+            double* d_dummy;
+            ENSURE("enn_dummy", nrep, d_dummy);
+            launch_vnn(bt.At, natot, d_ar, d_dummy, d_grad, ctx->stream);
+        }
+        CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+        const int grid_blocks = ctx->nsm * 4;
+        size_t scr = 0;
+        for (int cp = 0; cp < n_class_pairs(); cp++) scr = std::max(scr, grad2e_scratch_bytes(cp, grid_blocks * 128));
+        double* d_scr = nullptr;
+        if (scr) ENSURE("grad_scratch", scr / sizeof(double) + 1, d_scr);
+        for (int cp = 0; cp < n_class_pairs(); cp++) {
+            if (bt.tiles[cp].empty()) continue;
+            launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_grad, ctx->boys,
+                          o->schwarz_tau, d_scr, grid_blocks, ctx->stream);
+            ctx->stats.kernel_launches++;
+        }
+        CK(cudaEventRecord(ctx->ev[5], ctx->stream));
+        ctx->stats.kernel_launches += 3;
+    }
+    // MO cache
+    for (int r = 0; r < nrep; r++) {
+        auto& mo = ctx->mo[r];
+        const size_t bytes = sizeof(double) * bt.nbf[r] * bt.nbf[r];
+        if (mo.C.cap < bytes) {
+            if (mo.C.p) cudaFree(mo.C.p);
+            mo.C.p = nullptr;
+            mo.C.cap = 0;
+            if (cudaMalloc(&mo.C.p, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return set_err(ctx, PIMD_ENOMEM, "MO cache allocation failed");
+            }
+            mo.C.cap = bytes;
+        }
+        CK(cudaMemcpyAsync(mo.C.p, m.C + bt.moff[r], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        mo.Z.assign(Zc + bt.atom0[r], Zc + bt.atom0[r + 1]);
+        mo.N = bt.nbf[r];
+    }
+    CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+        ctx->stats.ms_total = ms;
+        if (o->want_gradient && d_grad) {
+            cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]);
+            ctx->stats.ms_grad2e = ms;
+        }
+    }
+    ctx->stats.nquartets_total = bt.nquart;
+    ctx->stats.eri_flops_per_build = bt.vrr_flops;
+    bool allconv = true;
+    for (int r = 0; r < nrep; r++) {
+        if (info) {
+            info[r].iterations = iters[r];
+            info[r].converged = conv[r];
+            info[r].final_dE = fdE[r];
+            info[r].final_error = ferr[r];
+            info[r].nquartets = bt.nquart_rep[r];
+        }
+        allconv = allconv && conv[r];
+    }
+    return allconv ? PIMD_OK : PIMD_ENOTCONV;
+}
+
+static int check_common(pimd_ctx* ctx, const pimd_basis* basis, const pimd_scf_opts* opts, pimd_scf_opts& o)
+{
+    if (!ctx || !basis) return PIMD_EINVAL;
+    pimd_scf_opts_default(&o);
+    if (opts) {
+        if (opts->struct_size < sizeof(size_t) || opts->struct_size > sizeof(pimd_scf_opts)) return PIMD_EINVAL;
+        memcpy(&o, opts, opts->struct_size);
+    }
+    if (!(o.conv_energy > 0) || !(o.conv_error > 0) || o.max_iter < 1 || o.max_iter > 10000 ||
+        !(o.schwarz_tau >= 0))
+        return set_err(ctx, PIMD_EINVAL, "bad SCF options");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    return PIMD_OK;
+}
+
+static int forces_impl(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc, const double* coords,
+                       bool coords_dev, const pimd_basis* basis, const pimd_scf_opts* opts, double* E,
+                       double* grad, bool out_dev, pimd_info* info, cudaStream_t user_stream)
+{
+    pimd_scf_opts o;
+    int rc = check_common(ctx, basis, opts, o);
+    if (rc) return rc;
+    if (nrep <= 0 || !natom_of || !Zc || !coords || !E) return set_err(ctx, PIMD_EINVAL, "bad sizes or pointers");
+    if (o.want_gradient && !grad) return set_err(ctx, PIMD_EINVAL, "gradients == NULL with want_gradient");
+    long long natot = 0;
+    for (int r = 0; r < nrep; r++) {
+        if (natom_of[r] <= 0 || natom_of[r] > 100000) return set_err(ctx, PIMD_EINVAL, "bad atom count");
+        natot += natom_of[r];
+    }
+    if (user_stream) CK(cudaStreamSynchronize(user_stream));
+    double* d_xyz;
+    ENSURE("xyz", natot * 3, d_xyz);
+    if (coords_dev) {
+        CK(cudaMemcpyAsync(d_xyz, coords, sizeof(double) * natot * 3, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        for (long long i = 0; i < natot * 3; i++)
+            if (!isfinite(coords[i])) return set_err(ctx, PIMD_EINVAL, "non-finite coordinates");
+        CK(cudaMemcpyAsync(d_xyz, coords, sizeof(double) * natot * 3, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    double *d_E, *d_g = nullptr;
+    ENSURE("out_E", nrep, d_E);
+    if (o.want_gradient) ENSURE("out_g", natot * 3, d_g);
+    rc = run_batch(ctx, nrep, natom_of, Zc, d_xyz, basis, &o, d_E, d_g, info);
+    if (rc && rc != PIMD_ENOTCONV) return rc;
+    const cudaMemcpyKind k = out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(E, d_E, sizeof(double) * nrep, k, ctx->stream));
+    if (o.want_gradient) CK(cudaMemcpyAsync(grad, d_g, sizeof(double) * natot * 3, k, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return rc;
+}
+
+extern "C" int pimd_bo_forces(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
+                              const pimd_basis* basis, const pimd_scf_opts* opts, double* energies,
+                              double* gradients, pimd_info* info)
+{
+    if (nrep <= 0 || natom <= 0 || !Z) return PIMD_EINVAL;
+    std::vector<int> nat(nrep, natom), Zc((size_t)nrep * natom);
+    for (int r = 0; r < nrep; r++) std::copy(Z, Z + natom, Zc.begin() + (size_t)r * natom);
+    return forces_impl(ctx, nrep, nat.data(), Zc.data(), coords, false, basis, opts, energies, gradients, false, info,
+                       nullptr);
+}
+
+extern "C" int string_images_forces(pimd_ctx* ctx, int nimg, const int* natom_of_img, const int* Z_concat,
+                                    const double* coords_concat, const pimd_basis* basis, const pimd_scf_opts* opts,
+                                    double* energies, double* gradients_concat, pimd_info* info)
+{
+    return forces_impl(ctx, nimg, natom_of_img, Z_concat, coords_concat, false, basis, opts, energies,
+                       gradients_concat, false, info, nullptr);
+}
+
+extern "C" int pimd_bo_forces_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords_dev,
+                                  const pimd_basis* basis, const pimd_scf_opts* opts, double* energies_dev,
+                                  double* gradients_dev, pimd_info* info, void* stream)
+{
+    if (nrep <= 0 || natom <= 0 || !Z) return PIMD_EINVAL;
+    std::vector<int> nat(nrep, natom), Zc((size_t)nrep * natom);
+    for (int r = 0; r < nrep; r++) std::copy(Z, Z + natom, Zc.begin() + (size_t)r * natom);
+    return forces_impl(ctx, nrep, nat.data(), Zc.data(), coords_dev, true, basis, opts, energies_dev, gradients_dev,
+                       true, info, (cudaStream_t)stream);
+}
+
+extern "C" int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* natom_of_img, const int* Z_concat,
+                                        const double* coords_concat_dev, const pimd_basis* basis,
+                                        const pimd_scf_opts* opts, double* energies_dev, double* gradients_concat_dev,
+                                        pimd_info* info, void* stream)
+{
+    return forces_impl(ctx, nimg, natom_of_img, Z_concat, coords_concat_dev, true, basis, opts, energies_dev,
+                       gradients_concat_dev, true, info, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// testing hooks
+// ---------------------------------------------------------------------------
+extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
+                             const pimd_basis* basis, double schwarz_tau, const double* D_dev, double* G_dev)
+{
+    if (!ctx || !basis || nrep <= 0 || natom <= 0 || !Z || !coords || !D_dev || !G_dev) return PIMD_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    std::vector<int> nat(nrep, natom), Zc((size_t)nrep * natom);
+    for (int r = 0; r < nrep; r++) std::copy(Z, Z + natom, Zc.begin() + (size_t)r * natom);
+    double* d_xyz;
+    ENSURE("xyz", (size_t)nrep * natom * 3, d_xyz);
+    CK(cudaMemcpyAsync(d_xyz, coords, sizeof(double) * nrep * natom * 3, cudaMemcpyHostToDevice, ctx->stream));
+    Batch bt;
+    int rc = setup_batch(ctx, bt, nrep, nat.data(), Zc.data(), d_xyz, basis, schwarz_tau);
+    if (rc) return rc;
+    Mats m;
+    if ((rc = alloc_mats(ctx, bt, m, 2))) return rc;
+    std::vector<int> active(nrep, 1);
+    UPLOAD("active", active, m.active);
+    bt.R.active = m.active;
+    CK(cudaMemcpyAsync(m.D, D_dev, sizeof(double) * bt.mtot, cudaMemcpyDeviceToDevice, ctx->stream));
+    if ((rc = fock_build(ctx, bt, m, schwarz_tau))) return rc;
+    // G_out = G' + G'^T
+    CK(cudaMemsetAsync(m.H, 0, sizeof(double) * bt.mtot, ctx->stream));
+    launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, nullptr, ctx->stream);
+    CK(cudaMemcpyAsync(G_dev, m.F, sizeof(double) * bt.mtot, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    ctx->stats.nquartets_total = bt.nquart;
+    ctx->stats.eri_flops_per_build = bt.vrr_flops;
+    return PIMD_OK;
+}
+
+extern "C" int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coords,
+                                 const pimd_basis* basis, double* S, double* T, double* V)
+{
+    if (!ctx || !basis || natom <= 0 || !Z || !coords || !S || !T || !V) return PIMD_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    double* d_xyz;
+    ENSURE("xyz", (size_t)natom * 3, d_xyz);
+    CK(cudaMemcpyAsync(d_xyz, coords, sizeof(double) * natom * 3, cudaMemcpyHostToDevice, ctx->stream));
+    Batch bt;
+    int nat = natom;
+    int rc = setup_batch(ctx, bt, 1, &nat, Z, d_xyz, basis, 1e-12);
+    if (rc) return rc;
+    Mats m;
+    if ((rc = alloc_mats(ctx, bt, m, 2))) return rc;
+    launch_one_electron(bt.P, bt.S, bt.B, bt.At, bt.R, m.S, m.T, m.V, ctx->boys, ctx->stream);
+    const size_t n = (size_t)bt.nbf[0] * bt.nbf[0];
+    CK(cudaMemcpyAsync(S, m.S, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(T, m.T, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(V, m.V, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    return PIMD_OK;
+}
+
+extern "C" int pimd_boys_dev(pimd_ctx* ctx, int n, int mord, const double* T_dev, double* F_dev)
+{
+    if (!ctx || n < 0 || mord < 0 || mord > BOYS_MMAX || (n > 0 && (!T_dev || !F_dev))) return PIMD_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    launch_boys_eval(n, mord, T_dev, F_dev, ctx->boys, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    return PIMD_OK;
+}

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of the C ABI in include/pimdgb.h (argument marshalling
+only: every step of the computation runs in the CUDA library).
+
+The library must have been built (`paper_1601_02713_gb300.build.build()` or
+`__graft_entry__.build()`); loading fails loudly otherwise. There is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ENOTCONV, PIMD_ETIMEOUT, PIMD_EBASIS = 0, -1, -2, -3, -4, -5, -6
+
+
+class PimdScfOpts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("conv_energy", ctypes.c_double),
+                ("conv_error", ctypes.c_double), ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int),
+                ("schwarz_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("guess", ctypes.c_int),
+                ("deterministic", ctypes.c_int), ("want_gradient", ctypes.c_int)]
+
+
+class PimdInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("final_dE", ctypes.c_double),
+                ("final_error", ctypes.c_double), ("nquartets", ctypes.c_longlong)]
+
+
+class PimdStats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("fock_builds", ctypes.c_int),
+                ("ms_fock", ctypes.c_double), ("ms_grad2e", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("nquartets_total", ctypes.c_longlong), ("eri_flops_per_build", ctypes.c_double)]
+
+
+class PimdError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    lib.pimd_scf_opts_default.argtypes = [ctypes.POINTER(PimdScfOpts)]
+    lib.pimd_scf_opts_default.restype = None
+    lib.pimd_ctx_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int]
+    lib.pimd_ctx_destroy.argtypes = [_P]
+    lib.pimd_ctx_destroy.restype = None
+    lib.pimd_ctx_clear_guess.argtypes = [_P]
+    lib.pimd_ctx_clear_guess.restype = None
+    lib.pimd_basis_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, _I, _I, _I, _I, _D, _D, ctypes.c_int]
+    lib.pimd_basis_destroy.argtypes = [_P]
+    lib.pimd_basis_destroy.restype = None
+    lib.pimd_basis_nbf.argtypes = [_P, ctypes.c_int, _I]
+    lib.pimd_bo_forces.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.POINTER(PimdScfOpts), _D, _D,
+                                   ctypes.POINTER(PimdInfo)]
+    lib.string_images_forces.argtypes = [_P, ctypes.c_int, _I, _I, _D, _P, ctypes.POINTER(PimdScfOpts), _D, _D,
+                                         ctypes.POINTER(PimdInfo)]
+    lib.pimd_bo_forces_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _P, _P, ctypes.POINTER(PimdScfOpts),
+                                       _P, _P, ctypes.POINTER(PimdInfo), _P]
+    lib.string_images_forces_dev.argtypes = [_P, ctypes.c_int, _I, _I, _P, _P, ctypes.POINTER(PimdScfOpts), _P, _P,
+                                             ctypes.POINTER(PimdInfo), _P]
+    lib.pimd_last_stats.argtypes = [_P, ctypes.POINTER(PimdStats)]
+    lib.pimd_fock_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.c_double, _P, _P]
+    lib.pimd_one_electron.argtypes = [_P, ctypes.c_int, _I, _D, _P, _D, _D, _D]
+    lib.pimd_boys_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
+    lib.pimd_peak_bench.argtypes = [ctypes.c_int, _D, _D, _D]
+    lib.pimd_strerror.argtypes = [ctypes.c_int]
+    lib.pimd_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().pimd_strerror(int(code)).decode()
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_I)
+
+
+def _check(rc, what, allow_notconv=False):
+    if rc == PIMD_OK or (allow_notconv and rc == PIMD_ENOTCONV):
+        return rc
+    raise PimdError(rc, what)
+
+
+def scf_opts(**kw) -> PimdScfOpts:
+    """Defaults of pimd_scf_opts_default, overridden by keyword."""
+    o = PimdScfOpts()
+    load().pimd_scf_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """pimd_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.handle = _P()
+        _check(load().pimd_ctx_create(ctypes.byref(self.handle), int(device)), "pimd_ctx_create")
+
+    def close(self):
+        if self.handle:
+            load().pimd_ctx_destroy(self.handle)
+            self.handle = _P()
+
+    def clear_guess(self):
+        load().pimd_ctx_clear_guess(self.handle)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Basis:
+    """pimd_basis from a per-element basis ({Z: [Shell(l, exps, coefs)]})."""
+
+    def __init__(self, basis: dict):
+        from .inputs import basis_arrays
+        Zs, nsh, sl, snp, ex, co = basis_arrays(basis)
+        self.handle = _P()
+        _check(load().pimd_basis_create(ctypes.byref(self.handle), len(Zs), _ip(Zs), _ip(nsh), _ip(sl), _ip(snp),
+                                        _dp(ex), _dp(co), 1), "pimd_basis_create")
+
+    def nbf(self, Z) -> int:
+        Z = np.ascontiguousarray(Z, np.int32)
+        n = load().pimd_basis_nbf(self.handle, len(Z), _ip(Z))
+        if n < 0:
+            raise PimdError(n, "pimd_basis_nbf")
+        return n
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().pimd_basis_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def _infos(arr):
+    return [dict(iterations=i.iterations, converged=i.converged, final_dE=i.final_dE, final_error=i.final_error,
+                 nquartets=i.nquartets) for i in arr]
+
+
+def pimd_bo_forces(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | None = None, check=True):
+    """Energies [nrep] and gradients [nrep, natom, 3] of nrep replicas of one
+    molecule (host arrays in and out). Returns (E, G, info, rc)."""
+    Z = np.ascontiguousarray(Z, np.int32)
+    X = np.ascontiguousarray(coords, np.float64)
+    nrep, natom = X.shape[0], X.shape[1]
+    opts = opts or scf_opts()
+    E = np.zeros(nrep)
+    G = np.zeros((nrep, natom, 3))
+    info = (PimdInfo * nrep)()
+    rc = load().pimd_bo_forces(ctx.handle, nrep, natom, _ip(Z), _dp(X), basis.handle, ctypes.byref(opts), _dp(E),
+                               _dp(G), info)
+    if check:
+        _check(rc, "pimd_bo_forces", allow_notconv=True)
+    return E, G, _infos(info), rc
+
+
+def string_images_forces(ctx: Context, basis: Basis, natom_of_img, Z_concat, coords_concat,
+                         opts: PimdScfOpts | None = None, check=True):
+    nat = np.ascontiguousarray(natom_of_img, np.int32)
+    Z = np.ascontiguousarray(Z_concat, np.int32)
+    X = np.ascontiguousarray(coords_concat, np.float64)
+    nimg = len(nat)
+    opts = opts or scf_opts()
+    E = np.zeros(nimg)
+    G = np.zeros((int(nat.sum()), 3))
+    info = (PimdInfo * nimg)()
+    rc = load().string_images_forces(ctx.handle, nimg, _ip(nat), _ip(Z), _dp(X), basis.handle, ctypes.byref(opts),
+                                     _dp(E), _dp(G), info)
+    if check:
+        _check(rc, "string_images_forces", allow_notconv=True)
+    return E, G, _infos(info), rc
+
+
+def pimd_bo_forces_dev(ctx: Context, basis: Basis, Z, coords_dev, energies_dev, gradients_dev,
+                       opts: PimdScfOpts | None = None, stream: int = 0, check=True):
+    """Device variant: coords/energies/gradients are CUDA tensors (float64,
+    contiguous) or raw device addresses."""
+    Z = np.ascontiguousarray(Z, np.int32)
+    nrep, natom = int(coords_dev.shape[0]), int(coords_dev.shape[1])
+    opts = opts or scf_opts()
+    info = (PimdInfo * nrep)()
+    rc = load().pimd_bo_forces_dev(ctx.handle, nrep, natom, _ip(Z), _P(coords_dev.data_ptr()), basis.handle,
+                                   ctypes.byref(opts), _P(energies_dev.data_ptr()),
+                                   _P(gradients_dev.data_ptr() if gradients_dev is not None else 0), info,
+                                   _P(stream))
+    if check:
+        _check(rc, "pimd_bo_forces_dev", allow_notconv=True)
+    return _infos(info), rc
+
+
+def string_images_forces_dev(ctx: Context, basis: Basis, natom_of_img, Z_concat, coords_dev, energies_dev,
+                             gradients_dev, opts: PimdScfOpts | None = None, stream: int = 0, check=True):
+    nat = np.ascontiguousarray(natom_of_img, np.int32)
+    Z = np.ascontiguousarray(Z_concat, np.int32)
+    opts = opts or scf_opts()
+    info = (PimdInfo * len(nat))()
+    rc = load().string_images_forces_dev(ctx.handle, len(nat), _ip(nat), _ip(Z), _P(coords_dev.data_ptr()),
+                                         basis.handle, ctypes.byref(opts), _P(energies_dev.data_ptr()),
+                                         _P(gradients_dev.data_ptr() if gradients_dev is not None else 0), info,
+                                         _P(stream))
+    if check:
+        _check(rc, "string_images_forces_dev", allow_notconv=True)
+    return _infos(info), rc
+
+
+def pimd_fock_dev(ctx: Context, basis: Basis, Z, coords, D_dev, G_dev, schwarz_tau: float = 1e-12):
+    """G = J - K/2 of a given density for nrep replicas (D, G device tensors
+    [nrep, N, N]); coords host [nrep, natom, 3]."""
+    Z = np.ascontiguousarray(Z, np.int32)
+    X = np.ascontiguousarray(coords, np.float64)
+    _check(load().pimd_fock_dev(ctx.handle, X.shape[0], X.shape[1], _ip(Z), _dp(X), basis.handle,
+                                float(schwarz_tau), _P(D_dev.data_ptr()), _P(G_dev.data_ptr())), "pimd_fock_dev")
+
+
+def pimd_one_electron(ctx: Context, basis: Basis, Z, coords):
+    Z = np.ascontiguousarray(Z, np.int32)
+    X = np.ascontiguousarray(coords, np.float64)
+    N = basis.nbf(Z)
+    S, T, V = np.zeros((N, N)), np.zeros((N, N)), np.zeros((N, N))
+    _check(load().pimd_one_electron(ctx.handle, len(Z), _ip(Z), _dp(X), basis.handle, _dp(S), _dp(T), _dp(V)),
+           "pimd_one_electron")
+    return S, T, V
+
+
+def pimd_boys_dev(ctx: Context, T_dev, m: int, F_dev):
+    _check(load().pimd_boys_dev(ctx.handle, int(T_dev.numel()), int(m), _P(T_dev.data_ptr()),
+                                _P(F_dev.data_ptr())), "pimd_boys_dev")
+
+
+def pimd_last_stats(ctx: Context) -> dict:
+    s = PimdStats()
+    _check(load().pimd_last_stats(ctx.handle, ctypes.byref(s)), "pimd_last_stats")
+    return {k: getattr(s, k) for k, _ in PimdStats._fields_}
+
+
+def pimd_peak_bench(device: int = 0) -> dict:
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().pimd_peak_bench(int(device), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "pimd_peak_bench")
+    return {"fp64_tflops": a.value, "fp32_tflops": b.value, "dmma_fp64_tflops": c.value}

@@ -1,0 +1,89 @@
+"""C-ABI library: it builds, loads without a GPU and exports every entry
+point that include/pimdgb.h declares; host-side argument checks."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1601_02713_gb300 import build as B
+from paper_1601_02713_gb300 import inputs, native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return native.load()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "pimdgb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["pimd_bo_forces", "string_images_forces", "pimd_ctx_create", "pimd_basis_create", "pimd_strerror"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_strerror_and_defaults(lib):
+    assert native.strerror(0) == "ok"
+    assert "invalid" in native.strerror(-1)
+    o = native.scf_opts()
+    assert o.struct_size == ctypes.sizeof(native.PimdScfOpts)
+    assert o.conv_energy == 1e-10 and o.conv_error == 1e-8 and o.schwarz_tau == 1e-12
+    assert o.max_iter == 64 and o.diis_size == 8 and o.want_gradient == 1
+
+
+def test_basis_create_and_validation(lib):
+    bas = inputs.basis_set("split_spd")
+    b = native.Basis(bas)
+    assert b.nbf([8, 1, 1]) == 24
+    assert b.nbf([6] * 9 + [1] * 12 + [8]) == 200
+    with pytest.raises(native.PimdError):
+        b.nbf([7])  # nitrogen is not in the basis
+    Zs, nsh, sl, snp, ex, co = inputs.basis_arrays(bas)
+    h = ctypes.c_void_p()
+    bad_l = sl.copy()
+    bad_l[0] = 3
+    rc = lib.pimd_basis_create(ctypes.byref(h), len(Zs), native._ip(Zs), native._ip(nsh), native._ip(bad_l),
+                               native._ip(snp), native._dp(ex), native._dp(co), 1)
+    assert rc == native.PIMD_EINVAL
+    bad_e = ex.copy()
+    bad_e[2] = -1.0
+    rc = lib.pimd_basis_create(ctypes.byref(h), len(Zs), native._ip(Zs), native._ip(nsh), native._ip(sl),
+                               native._ip(snp), native._dp(bad_e), native._dp(co), 1)
+    assert rc == native.PIMD_EINVAL
+    rc = lib.pimd_basis_create(ctypes.byref(h), len(Zs), native._ip(Zs), native._ip(nsh), native._ip(sl),
+                               native._ip(snp), native._dp(ex), native._dp(co), 0)
+    assert rc == native.PIMD_EINVAL
+
+
+def test_forces_reject_null_context(lib):
+    Z = np.array([8, 1, 1], np.int32)
+    X = np.zeros((1, 3, 3))
+    E = np.zeros(1)
+    G = np.zeros((1, 3, 3))
+    rc = lib.pimd_bo_forces(None, 1, 3, native._ip(Z), native._dp(X), None, None, native._dp(E), native._dp(G), None)
+    assert rc == native.PIMD_EINVAL
+
+
+def test_generated_sources_are_deterministic():
+    g = B._gen_module()
+    import tempfile
+    with tempfile.TemporaryDirectory() as d1, tempfile.TemporaryDirectory() as d2:
+        g.generate(d1)
+        g.generate(d2)
+        for f in sorted(os.listdir(d1)):
+            assert open(os.path.join(d1, f)).read() == open(os.path.join(d2, f)).read(), f

@@ -1,0 +1,154 @@
+"""GPU parity against the CPU oracle, through the C ABI.
+
+Bars (the tolerances of the FP64 path): energies within 1e-8 hartree,
+gradients within 1e-6 hartree/bohr of the oracle; intermediate quantities
+(Boys values, one-electron matrices, Fock matrices of a fixed density) within
+the round-off of FP64 sums of their size.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_02713_gb300 import inputs, native
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+E_TOL = 1e-8
+G_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return native.Context(0)
+
+
+@pytest.fixture(scope="module")
+def spd():
+    bas = inputs.basis_set("split_spd")
+    return bas, native.Basis(bas)
+
+
+def test_boys_function(ctx):
+    rng = np.random.default_rng(0)
+    T = np.concatenate([np.linspace(0, 45, 721), rng.uniform(0, 60, 2000), [1e-12, 39.999, 40.0, 40.001, 150.0]])
+    Tt = torch.tensor(T, dtype=torch.float64, device="cuda")
+    for m in [0, 1, 2, 5, 9, 12]:
+        F = torch.empty_like(Tt)
+        native.pimd_boys_dev(ctx, Tt, m, F)
+        got = F.cpu().numpy()
+        ref = np.array([O.boys(m, t) for t in T])
+        rel = np.abs(got - ref) / ref
+        assert rel.max() < 5e-14, (m, rel.max(), T[rel.argmax()])
+
+
+@pytest.mark.parametrize("mol", ["water", "dimer"])
+def test_one_electron_matrices(ctx, spd, mol):
+    bas, B = spd
+    if mol == "water":
+        Z, X = inputs.small_molecule("water")
+    else:
+        r, _ = inputs.workload("water2_min_4beads")
+        Z, Xs = r.stacked()
+        X = Xs[1]
+    S, T, V = native.pimd_one_electron(ctx, B, Z, X)
+    ob = O.OracleBasis.build(bas, Z, X)
+    S0, T0, V0 = O.one_electron(ob, Z, X)
+    np.testing.assert_allclose(S, S0, atol=1e-13)
+    np.testing.assert_allclose(T, T0, atol=1e-11)
+    np.testing.assert_allclose(V, V0, atol=1e-11)
+
+
+def _random_density(N, nrep, seed):
+    rng = np.random.default_rng(seed)
+    D = rng.normal(size=(nrep, N, N)) * 0.3
+    return D + D.transpose(0, 2, 1)
+
+
+@pytest.mark.parametrize("mol,nrep", [("water", 1), ("water2_spd", 3)])
+def test_fock_matrix_of_fixed_density(ctx, spd, mol, nrep):
+    bas, B = spd
+    if mol == "water":
+        Z, X = inputs.small_molecule("water")
+        Xs = np.stack([X] * nrep)
+    else:
+        r, _ = inputs.workload("water2_min_4beads", nrep=nrep)
+        Z, Xs = r.stacked()
+    N = B.nbf(Z)
+    D = _random_density(N, nrep, 7)
+    Dt = torch.tensor(D, device="cuda")
+    Gt = torch.zeros_like(Dt)
+    native.pimd_fock_dev(ctx, B, Z, Xs, Dt, Gt, 1e-12)
+    G = Gt.cpu().numpy()
+    for k in range(nrep):
+        ob = O.OracleBasis.build(bas, Z, Xs[k])
+        J, K, _ = O.jk(ob, D[k], 1e-12)
+        ref = J - 0.5 * K
+        err = np.abs(G[k] - ref).max()
+        assert err < 1e-10 * max(1.0, np.abs(ref).max()), (k, err)
+
+
+def _oracle_eg(bas, Z, X):
+    E, G, res = O.rhf_energy_gradient(bas, Z, X)
+    assert res.converged
+    return E, G
+
+
+def test_water_dimer_min_basis_4_beads(ctx):
+    reps, kind = inputs.workload("water2_min_4beads")
+    Z, Xs = reps.stacked()
+    bas = inputs.basis_set(kind)
+    B = native.Basis(bas)
+    E, G, info, rc = native.pimd_bo_forces(ctx, B, Z, Xs)
+    assert rc == 0
+    for k in range(len(Xs)):
+        E0, G0 = _oracle_eg(bas, Z, Xs[k])
+        assert abs(E[k] - E0) < E_TOL, (k, E[k], E0)
+        assert np.abs(G[k] - G0).max() < G_TOL, (k, np.abs(G[k] - G0).max())
+        assert info[k]["converged"] == 1
+
+
+def test_water_monomer_spd(ctx, spd):
+    bas, B = spd
+    Z, X = inputs.small_molecule("water")
+    E, G, info, rc = native.pimd_bo_forces(ctx, B, Z, X[None])
+    assert rc == 0
+    E0, G0 = _oracle_eg(bas, Z, X)
+    assert abs(E[0] - E0) < E_TOL
+    assert np.abs(G[0] - G0).max() < G_TOL
+    assert np.abs(G[0].sum(0)).max() < 1e-9
+
+
+def test_batched_equals_single(ctx, spd):
+    bas, B = spd
+    reps, _ = inputs.workload("water2_min_4beads", nrep=3)
+    Z, Xs = reps.stacked()
+    E, G, _, rc = native.pimd_bo_forces(ctx, B, Z, Xs)
+    assert rc == 0
+    for k in range(3):
+        e1, g1, _, rc1 = native.pimd_bo_forces(ctx, B, Z, Xs[k:k + 1])
+        assert rc1 == 0
+        assert abs(e1[0] - E[k]) < 1e-11
+        assert np.abs(g1[0] - G[k]).max() < 1e-10
+
+
+def test_ragged_images(ctx, spd):
+    bas, B = spd
+    Zw, Xw = inputs.small_molecule("water")
+    r, _ = inputs.workload("water2_min_4beads", nrep=2)
+    Zd, Xd = r.stacked()
+    mols = [(Zw, Xw), (Zd, Xd[0]), (Zw, Xw + 0.05), (Zd, Xd[1])]
+    nat = [len(z) for z, _ in mols]
+    Zc = np.concatenate([z for z, _ in mols])
+    Xc = np.concatenate([x for _, x in mols])
+    E, G, info, rc = native.string_images_forces(ctx, B, nat, Zc, Xc)
+    assert rc == 0
+    off = 0
+    for k, (z, x) in enumerate(mols):
+        E0, G0 = _oracle_eg(bas, z, x)
+        assert abs(E[k] - E0) < E_TOL, (k, E[k] - E0)
+        assert np.abs(G[off:off + len(z)] - G0).max() < G_TOL
+        off += len(z)
