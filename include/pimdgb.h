@@ -137,8 +137,11 @@ typedef struct {
     double ms_fock;
     double ms_grad2e;
     double ms_total;
-    long long nquartets_total;   /* screened quartets over all replicas, per Fock build */
-    double eri_flops_per_build;  /* counted FP64 operations of the VRR per Fock build (all replicas) */
+    long long nquartets_total;   /* Schwarz-screened quartets over all replicas (full build) */
+    double eri_flops_per_build;  /* executed floating-point operations of the primitive loop per Fock build,
+                                    averaged over the call's builds (generated recursion + per-primitive
+                                    set-up and Boys, counted from the generated code), all replicas */
+    double eris_per_build;       /* executed unique contracted basis-function ERIs per Fock build (average) */
 } pimd_stats;
 int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
 

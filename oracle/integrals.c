@@ -812,3 +812,52 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Timing samples for the CPU baseline: the same contracted blocks as above  */
+/* for a caller-given list of shell quartets (4 ints each); returns the sum  */
+/* of |values| so that the work cannot be skipped.                           */
+/* ------------------------------------------------------------------------- */
+double oracle_eri_list(BASIS_ARGS, int nq, const int *quartets)
+{
+    MAKE_BASIS;
+    double total = 0.0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : total)
+    for (int q = 0; q < nq; q++) {
+        double blk[BLK];
+        const int *s = quartets + 4 * q;
+        eri_block(&bs, s[0], s[1], s[2], s[3], blk);
+        int n = shell_nbf(&bs, s[0]) * shell_nbf(&bs, s[1]) * shell_nbf(&bs, s[2]) * shell_nbf(&bs, s[3]);
+        for (int x = 0; x < n; x++) total += fabs(blk[x]);
+    }
+    return total;
+}
+
+/* derivative blocks (raised and lowered on each of the four centres, as in
+ * oracle_grad_2e) for a list of quartets */
+double oracle_deriv_list(BASIS_ARGS, int nq, const int *quartets)
+{
+    MAKE_BASIS;
+    double total = 0.0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : total)
+    for (int q = 0; q < nq; q++) {
+        double *up = malloc(sizeof(double) * BLK), *dn = malloc(sizeof(double) * BLK);
+        const int *sh = quartets + 4 * q;
+        for (int k = 0; k < 4; k++) {
+            int dl[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
+            dl[k] = 1;
+            w[k] = 1;
+            eri_contracted_cart(&bs, sh, dl, w, up);
+            total += fabs(up[0]);
+            if (bs.l[sh[k]] > 0) {
+                dl[k] = -1;
+                w[k] = 0;
+                eri_contracted_cart(&bs, sh, dl, w, dn);
+                total += fabs(dn[0]);
+            }
+        }
+        free(up);
+        free(dn);
+    }
+    return total;
+}

@@ -68,6 +68,10 @@ def _load():
         lib.oracle_one_electron.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.oracle_grad_1e.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_eri_list.argtypes = basis + [ctypes.c_int, ip]
+        lib.oracle_eri_list.restype = ctypes.c_double
+        lib.oracle_deriv_list.argtypes = basis + [ctypes.c_int, ip]
+        lib.oracle_deriv_list.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -207,6 +211,33 @@ def grad_1e(ob: OracleBasis, Z, xyz, D, W):
     _load().oracle_grad_1e(*ob.args(), natom, _dp(Zn), _dp(C), _dp(np.ascontiguousarray(D, float)),
                            _dp(np.ascontiguousarray(W, float)), _dp(g))
     return g
+
+
+def eri_list(ob: OracleBasis, quartets) -> float:
+    """Contracted blocks of the listed shell quartets (timing samples)."""
+    q = np.ascontiguousarray(quartets, np.int32)
+    return _load().oracle_eri_list(*ob.args(), len(q), _ip(q))
+
+
+def deriv_list(ob: OracleBasis, quartets) -> float:
+    """Derivative blocks of the listed shell quartets (timing samples)."""
+    q = np.ascontiguousarray(quartets, np.int32)
+    return _load().oracle_deriv_list(*ob.args(), len(q), _ip(q))
+
+
+def canonical_quartets(ob: OracleBasis, tau: float = 1e-12):
+    """All canonical shell quartets (a>=b, c>=d, ab>=cd) with Q_ab Q_cd >= tau,
+    as an [n, 4] int array (pair order as in oracle_jk)."""
+    Q = schwarz(ob)
+    ns = len(ob.l)
+    a, b = np.tril_indices(ns)
+    qp = Q[a, b]
+    out = []
+    for i in range(len(a)):
+        j = np.nonzero(qp[: i + 1] * qp[i] >= tau)[0]
+        if len(j):
+            out.append(np.stack([np.full(len(j), a[i]), np.full(len(j), b[i]), a[j], b[j]], axis=1))
+    return np.concatenate(out).astype(np.int32)
 
 
 def nuclear_repulsion(Z, xyz):

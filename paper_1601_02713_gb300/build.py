@@ -72,9 +72,10 @@ def generate_sources():
         e = ['#include "eri_kernels.cuh"', '#include "internal.h"', f'#include "eri_{nm}.cuh"',
              "namespace pimd {",
              f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-             "                     const double* D, double* G, const double* boys, double tau, cudaStream_t st)",
+             "                     const double* D, double* G, const double* boys, double tau, const double* Dsh,",
+             "                     unsigned long long* cnt, cudaStream_t st)",
              "{",
-             f"    if (ntiles > 0) jk_kernel<Cls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, G, boys, tau);",
+             f"    if (ntiles > 0) jk_kernel<Cls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, G, boys, tau, Dsh, cnt);",
              "}"]
         if same:
             e += [f"void launch_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
@@ -95,9 +96,9 @@ def generate_sources():
                    f"size_t grad2e_scratch_{nm}(int) {{ return 0; }}",
                    f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                    "                        const double* D, double* grad, const double* boys, double tau, double*, int,",
-                   "                        cudaStream_t st)",
+                   "                        const double* Dsh, cudaStream_t st)",
                    "{",
-                   f"    if (ntiles > 0) grad2e_kernel<GCls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boys, tau);",
+                   f"    if (ntiles > 0) grad2e_kernel<GCls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boys, tau, Dsh);",
                    "}"]
         else:
             gl += ["static TapeDev g_tape[64];",
@@ -132,13 +133,13 @@ def generate_sources():
                    f"size_t grad2e_scratch_{nm}(int threads) {{ return (size_t)Tape_{nm}::NSLOT * threads * sizeof(double); }}",
                    f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                    "                        const double* D, double* grad, const double* boys, double tau,",
-                   "                        double* scratch, int grid_blocks, cudaStream_t st)",
+                   "                        double* scratch, int grid_blocks, const double* Dsh, cudaStream_t st)",
                    "{",
                    f"    grad2e_upload_{nm}();",
                    "    int dev = 0;",
                    "    cudaGetDevice(&dev);",
                    f"    if (ntiles > 0) grad2e_tape_kernel<GCls_{nm}><<<grid_blocks, 128, 0, st>>>(P, S, R, tiles, ntiles, D,",
-                   "        grad, boys, tau, g_tape[dev], scratch);",
+                   "        grad, boys, tau, g_tape[dev], scratch, Dsh);",
                    "}"]
         gl.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_grad_{nm}.cu")
@@ -147,10 +148,10 @@ def generate_sources():
     # dispatch
     d = ['#include "internal.h"', "namespace pimd {"]
     sig_jk = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-              "double, cudaStream_t")
+              "double, const double*, unsigned long long*, cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-             "double, double*, int, cudaStream_t")
+             "double, double*, int, const double*, cudaStream_t")
     for c, nm in zip(classes, names):
         d.append(f"void launch_jk_{nm}({sig_jk});")
         if (c[0], c[1]) == (c[2], c[3]):
@@ -167,14 +168,19 @@ def generate_sources():
     flops = {s[0]: s[2] for s in stats}
     d.append("long long class_vrr_flops(int cp)")
     d.append("{")
-    d.append("    static const long long t[] = {" + ", ".join(str(flops[nm]) for nm in names) + "};")
+    # per primitive quartet: the generated recursion's operations plus the
+    # set-up of prim_quartet (41), the Boys Taylor step and recursion (19 + 2L)
+    # and the prefactor scaling (L + 1)
+    d.append("    static const long long t[] = {" + ", ".join(str(flops[nm] + 61 + 3 * sum(c))
+                                                        for c, nm in zip(classes, names)) + "};")
     d.append("    return t[cp];")
     d.append("}")
     d.append(f"typedef void (*JkFn)({sig_jk});")
     d.append("static const JkFn jk_tab[] = {" + ", ".join(f"launch_jk_{nm}" for nm in names) + "};")
     d.append("void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
-             "const double* D, double* G, const double* boys, double tau, cudaStream_t st)")
-    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, G, boys, tau, st); }")
+             "const double* D, double* G, const double* boys, double tau, const double* Dsh, unsigned long long* cnt, "
+             "cudaStream_t st)")
+    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, G, boys, tau, Dsh, cnt, st); }")
     same = [nm for c, nm in zip(classes, names) if (c[0], c[1]) == (c[2], c[3])]
     d.append(f"typedef void (*SwFn)({sig_sw});")
     d.append("static const SwFn sw_tab[] = {" + ", ".join(f"launch_schwarz_{nm}" for nm in same) + "};")
@@ -188,8 +194,8 @@ def generate_sources():
     d.append("size_t grad2e_scratch_bytes(int cp, int threads) { return gs_tab[cp](threads); }")
     d.append("void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, double* grad, const double* boys, double tau, double* scratch, int grid_blocks, "
-             "cudaStream_t st)")
-    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, tau, scratch, grid_blocks, st); }")
+             "const double* Dsh, cudaStream_t st)")
+    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, tau, scratch, grid_blocks, Dsh, st); }")
     d.append("void grad2e_tapes_upload() {")
     for nm in names:
         d.append(f"    grad2e_upload_{nm}();")

@@ -278,7 +278,8 @@ __device__ __forceinline__ void quartet_cart(const double (*sbra)[PIMD_MAXPP], i
 template <class C>
 __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
                                                  const double* __restrict__ Dall, double* __restrict__ Gall,
-                                                 const double* __restrict__ boys, double tau)
+                                                 const double* __restrict__ boys, double tau,
+                                                 const double* __restrict__ Dsh, unsigned long long* __restrict__ cnt)
 {
     __shared__ double sbra[6][PIMD_MAXPP];
     const Tile t = tiles[blockIdx.x];
@@ -290,10 +291,29 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R, cons
     }
     __syncthreads();
     const int cd = t.c0 + threadIdx.x;
-    if (cd >= t.c1) return;
-    const double Qab = P.Q[ab], Qcd = P.Q[cd];
-    if (Qab * Qcd < tau) return;
-    const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
+    const int r = t.rep;
+    bool work = cd < t.c1;
+    int sa = 0, sb = 0, sc = 0, sd = 0;
+    if (work) {
+        sa = P.sa[ab];
+        sb = P.sb[ab];
+        sc = P.sa[cd];
+        sd = P.sb[cd];
+        // density-weighted Schwarz bound: every contribution of the quartet to
+        // G' is at most 2 |(ab|cd)| times one of these six density blocks
+        const double dq = fmax(fmax(fmax(shell_bound(R, Dsh, r, sa, sb), shell_bound(R, Dsh, r, sc, sd)),
+                                    fmax(shell_bound(R, Dsh, r, sa, sc), shell_bound(R, Dsh, r, sa, sd))),
+                               fmax(shell_bound(R, Dsh, r, sb, sc), shell_bound(R, Dsh, r, sb, sd)));
+        work = P.Q[ab] * P.Q[cd] * dq >= tau;
+    }
+    // executed quartets and primitive quartets of this class (work counters)
+    const unsigned nq = __reduce_add_sync(0xffffffffu, work ? 1u : 0u);
+    const unsigned np = __reduce_add_sync(0xffffffffu, work ? (unsigned)(P.npp[ab] * P.npp[cd]) : 0u);
+    if ((threadIdx.x & 31) == 0 && nq) {
+        atomicAdd(cnt, (unsigned long long)nq);
+        atomicAdd(cnt + 1, (unsigned long long)np);
+    }
+    if (!work) return;
     double A[3], B[3], Cc[3], Dd[3];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
@@ -310,7 +330,6 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R, cons
     if (sa == sb) f *= 0.5;
     if (sc == sd) f *= 0.5;
     if (ab == cd) f *= 0.5;
-    const int r = t.rep;
     const int N = R.nbf[r];
     const size_t off = R.moff[r];
     scatter_jk<C::LA, C::LB, C::LC, C::LD>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,

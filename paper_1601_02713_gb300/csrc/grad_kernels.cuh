@@ -127,11 +127,21 @@ __device__ __forceinline__ void scatter_grad(double* grad, const Shells& S, int 
     }
 }
 
+// bound of |Gamma| over a quartet from the shell-pair density bounds
+__device__ __forceinline__ double gamma_bound(const Reps& R, const double* Dsh, int r, int sa, int sb, int sc, int sd)
+{
+    const double j = shell_bound(R, Dsh, r, sa, sb) * shell_bound(R, Dsh, r, sc, sd);
+    const double k1 = shell_bound(R, Dsh, r, sa, sc) * shell_bound(R, Dsh, r, sb, sd);
+    const double k2 = shell_bound(R, Dsh, r, sa, sd) * shell_bound(R, Dsh, r, sb, sc);
+    return 4.0 * j + k1 + k2;
+}
+
 // Straight-line gradient kernel (generated VRR/HRR), blockDim.x == 128.
 template <class G>
 __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
                                                      const double* __restrict__ Dall, double* __restrict__ grad,
-                                                     const double* __restrict__ boys, double tau)
+                                                     const double* __restrict__ boys, double tau,
+                                                     const double* __restrict__ Dsh)
 {
     constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
     __shared__ double sbra[8][PIMD_MAXPP];
@@ -144,8 +154,8 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, 
     __syncthreads();
     const int cd = t.c0 + threadIdx.x;
     if (cd >= t.c1) return;
-    if (P.Q[ab] * P.Q[cd] < tau) return;
     const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
+    if (P.Q[ab] * P.Q[cd] * gamma_bound(R, Dsh, t.rep, sa, sb, sc, sd) < tau) return;
     double A[3], B[3], Cc[3], Dd[3];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
@@ -250,7 +260,8 @@ template <class G>
 __global__ void __launch_bounds__(128) grad2e_tape_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
                                                           int ntiles, const double* __restrict__ Dall,
                                                           double* __restrict__ grad, const double* __restrict__ boys,
-                                                          double tau, TapeDev tp, double* __restrict__ scratch)
+                                                          double tau, TapeDev tp, double* __restrict__ scratch,
+                                                          const double* __restrict__ Dsh)
 {
     constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
     __shared__ double sbra[8][PIMD_MAXPP];
@@ -267,8 +278,8 @@ __global__ void __launch_bounds__(128) grad2e_tape_kernel(Pairs P, Shells S, Rep
         __syncthreads();
         const int cd = t.c0 + threadIdx.x;
         if (cd >= t.c1) continue;
-        if (P.Q[ab] * P.Q[cd] < tau) continue;
         const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
+        if (P.Q[ab] * P.Q[cd] * gamma_bound(R, Dsh, t.rep, sa, sb, sc, sd) < tau) continue;
         double A[3], B[3], Cc[3], Dd[3];
 #pragma unroll
         for (int x = 0; x < 3; x++) {

@@ -42,16 +42,19 @@ void launch_vnn(const AtomsDev& At, int natom_total, const int* atom_rep, double
 // ss, ps, pp, ds, dp, dd)
 int n_class_pairs();
 void class_pair_ls(int cp, int* la, int* lb, int* lc, int* ld);
+// floating-point operations per primitive quartet of class pair cp: the
+// generated recursion plus per-primitive set-up, Boys and prefactor
 long long class_vrr_flops(int cp);
 void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
-               const double* D, double* G, const double* boys, double tau, cudaStream_t st);
+               const double* D, double* G, const double* boys, double tau, const double* Dsh,
+               unsigned long long* cnt, cudaStream_t st);
 void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n, const double* boys,
                     double* Q, cudaStream_t st);
 // gradient: returns scratch bytes the tape path needs for class pair cp (0 if straight-line)
 size_t grad2e_scratch_bytes(int cp, int grid_threads);
 void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                    const double* D, double* grad, const double* boys, double tau, double* scratch,
-                   int grid_blocks, cudaStream_t st);
+                   int grid_blocks, const double* Dsh, cudaStream_t st);
 void grad2e_tapes_upload();   // once per device
 void boys_table_upload(double** dev_tab);
 
@@ -99,9 +102,17 @@ void launch_diis_combine(const RepMat* rm, int nrep, const double* Fh, const dou
                          const double* F, double* Fbar, const int* diis_on, const int* active, cudaStream_t st);
 void launch_copy_mats(const RepMat* rm, int nrep, const double* src, double* dst, const int* mask,
                       cudaStream_t st);
+void launch_identity(const RepMat* rm, int nrep, double* A, const int* mask, cudaStream_t st);
 void launch_boys_eval(int n, int m, const double* T, double* F, const double* boys, cudaStream_t st);
 void gather_xyz(const double* atom_xyz, const int* shell_atom, int nshell, double* shell_xyz, cudaStream_t st);
 void add_mats(const RepMat* rm, int nrep, const double* A, const double* B, double* C, cudaStream_t st);
 void diis_set_stride(long long stride);
+// shell-pair bounds Dsh[r][a][b] = max |M_mn| over the block (replicas in mask)
+void launch_shell_bounds(const Shells& S, const Reps& R, int nrep, int maxsh, const double* M, double* Dsh,
+                         const int* mask, cudaStream_t st);
+// incremental Fock build: dD = D - Dprev (mode 1) or D (mode 2), G zeroed for
+// mode 2, Dprev <- D; mode 0 replicas untouched
+void launch_delta_density(const RepMat* rm, int nrep, const double* D, double* Dprev, double* dD, double* G,
+                          const int* mode, cudaStream_t st);
 
 }  // namespace pimd

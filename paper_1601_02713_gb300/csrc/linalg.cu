@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* __restrict__ 
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
 // g_p <- c g_p - s g_q, g_q <- s g_p + c g_q.
 // ---------------------------------------------------------------------------
-constexpr int JAC_THREADS = 512;
+constexpr int JAC_THREADS = 1024;
 constexpr int JAC_MAXSWEEP = 60;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -429,6 +429,15 @@ __global__ void diis_combine_kernel(const RepMat* rms, const double* Fh, const d
     }
 }
 
+__global__ void identity_kernel(const RepMat* rms, double* A, const int* mask)
+{
+    const int r = blockIdx.y;
+    if (mask && !mask[r]) return;
+    const RepMat rm = rms[r];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rm.N * rm.N; e += gridDim.x * blockDim.x)
+        A[rm.off + e] = (e / rm.N == e % rm.N) ? 1.0 : 0.0;
+}
+
 __global__ void gather_xyz_kernel(const double* ax, const int* sa, int n, double* sx)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -444,14 +453,68 @@ __global__ void add_mats_kernel(const RepMat* rms, const double* A, const double
         C[rm.off + e] = A[rm.off + e] + B[rm.off + e];
 }
 
+__global__ void shell_bounds_kernel(Shells S, Reps R, const double* M, double* Dsh, const int* mask)
+{
+    const int r = blockIdx.y;
+    if (mask && !mask[r]) return;
+    const int n = R.nsh[r];
+    const int a = blockIdx.x;
+    if (a >= n) return;
+    const int N = R.nbf[r];
+    const double* m = M + R.moff[r];
+    const int ga = R.sh0[r] + a;
+    const int fa = S.bf[ga], na = nsph(S.l[ga]);
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const int gb = R.sh0[r] + b;
+        const int fb = S.bf[gb], nb = nsph(S.l[gb]);
+        double mx = 0.0;
+        for (int i = 0; i < na; i++)
+            for (int j = 0; j < nb; j++) mx = fmax(mx, fabs(m[(size_t)(fa + i) * N + fb + j]));
+        Dsh[R.dsoff[r] + (size_t)a * n + b] = mx;
+    }
+}
+
+__global__ void delta_density_kernel(const RepMat* rms, const double* D, double* Dprev, double* dD, double* G,
+                                     const int* mode)
+{
+    const int r = blockIdx.y;
+    const int md = mode[r];
+    if (md == 0) return;
+    const RepMat rm = rms[r];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rm.N * rm.N; e += gridDim.x * blockDim.x) {
+        const double d = D[rm.off + e];
+        dD[rm.off + e] = md == 1 ? d - Dprev[rm.off + e] : d;
+        Dprev[rm.off + e] = d;
+        if (md == 2) G[rm.off + e] = 0.0;
+    }
+}
+
 }  // namespace
 
 static long long g_diis_stride = 0;
+
+void launch_shell_bounds(const Shells& S, const Reps& R, int nrep, int maxsh, const double* M, double* Dsh,
+                         const int* mask, cudaStream_t st)
+{
+    if (nrep == 0 || maxsh == 0) return;
+    shell_bounds_kernel<<<dim3(maxsh, nrep), 128, 0, st>>>(S, R, M, Dsh, mask);
+}
+
+void launch_delta_density(const RepMat* rm, int nrep, const double* D, double* Dprev, double* dD, double* G,
+                          const int* mode, cudaStream_t st)
+{
+    delta_density_kernel<<<dim3(64, nrep), 256, 0, st>>>(rm, D, Dprev, dD, G, mode);
+}
 
 void gather_xyz(const double* atom_xyz, const int* shell_atom, int nshell, double* shell_xyz, cudaStream_t st)
 {
     if (nshell == 0) return;
     gather_xyz_kernel<<<(nshell + 127) / 128, 128, 0, st>>>(atom_xyz, shell_atom, nshell, shell_xyz);
+}
+
+void launch_identity(const RepMat* rm, int nrep, double* A, const int* mask, cudaStream_t st)
+{
+    identity_kernel<<<dim3(64, nrep), 256, 0, st>>>(rm, A, mask);
 }
 
 void add_mats(const RepMat* rm, int nrep, const double* A, const double* B, double* C, cudaStream_t st)

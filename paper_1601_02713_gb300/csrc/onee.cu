@@ -244,17 +244,27 @@ __global__ void pair_data_kernel(Pairs P, int* npp, double* pp, Shells S, BasisP
         AB2 += (A[x] - Bc[x]) * (A[x] - Bc[x]);
     }
     const double c0 = 1.4142135623730950488 * pow(kPi, 1.25);
+    // primitive pairs whose prefactor is below 1e-17 of the pair's largest
+    // one are dropped (their share of any integral is below double rounding)
+    double kmax = 0.0;
+    for (int i = 0; i < na; i++)
+        for (int j = 0; j < nb; j++) {
+            const double ea = B.exps[pa + i], eb = B.exps[pb + j];
+            kmax = fmax(kmax, fabs(B.coefs[pa + i] * B.coefs[pb + j] * exp(-ea * eb / (ea + eb) * AB2) / (ea + eb)));
+        }
     int k = 0;
     for (int i = 0; i < na; i++)
         for (int j = 0; j < nb; j++) {
             const double ea = B.exps[pa + i], eb = B.exps[pb + j];
             const double p = ea + eb, ip = 1.0 / p;
+            const double kij = B.coefs[pa + i] * B.coefs[pb + j] * exp(-ea * eb * ip * AB2) * ip;
+            if (fabs(kij) < 1e-17 * kmax) continue;
             const double vals[PP_NF] = {p,
                                         ip,
                                         (ea * A[0] + eb * Bc[0]) * ip,
                                         (ea * A[1] + eb * Bc[1]) * ip,
                                         (ea * A[2] + eb * Bc[2]) * ip,
-                                        c0 * B.coefs[pa + i] * B.coefs[pb + j] * exp(-ea * eb * ip * AB2) * ip,
+                                        c0 * kij,
                                         ea,
                                         eb};
             for (int f = 0; f < PP_NF; f++) pp[((size_t)f * PIMD_MAXPP + k) * P.n + g] = vals[f];

@@ -54,7 +54,17 @@ struct Reps {
     const int* nbf;             // functions per replica
     const long long* moff;      // offset of the replica's N x N matrices
     const int* active;          // 1 while the replica's SCF runs
+    const int* sh0;             // first (global) shell of each replica
+    const int* nsh;             // shells per replica
+    const long long* dsoff;     // offset of the replica's nsh x nsh shell-pair density bounds
 };
+
+// max |M_mn| over the functions of shells (a, b) of replica r (global shell ids)
+__device__ __forceinline__ double shell_bound(const Reps& R, const double* __restrict__ Dsh, int r, int a, int b)
+{
+    const int a0 = R.sh0[r], n = R.nsh[r];
+    return __ldg(Dsh + R.dsoff[r] + (size_t)(a - a0) * n + (b - a0));
+}
 
 // one block of quartets: bra pair ab with ket pairs [c0, c1)
 struct Tile {

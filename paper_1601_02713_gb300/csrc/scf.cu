@@ -320,6 +320,12 @@ struct Batch {
     // shells
     std::vector<int> sh_l, sh_bf, sh_atom, sh_rep, sh_prim, sh_nprim;
     std::vector<int> rep_sh0;
+    std::vector<int> nsh_rep;
+    std::vector<long long> dsoff;
+    int maxsh = 0;
+    double* Dsh = nullptr;
+    std::vector<int> npp;
+    unsigned long long* cnt = nullptr;   // [2 * class pairs]: executed quartets, primitive quartets
     // pairs grouped by (rep, class)
     std::vector<int> pa, pb;
     std::vector<int> grp0;   // [nrep * 6 + 1] start of group (rep, X)
@@ -329,6 +335,7 @@ struct Batch {
     long long nquart = 0;
     std::vector<long long> nquart_rep;
     double vrr_flops = 0.0;
+    double eris = 0.0;
     // device views
     Pairs P{};
     Shells S{};
@@ -464,7 +471,25 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     UPLOAD("moff", bt.moff, d_moff);
     int* d_active;
     ENSURE("active", nrep, d_active);
-    bt.R = Reps{d_nbf, d_moff, d_active};
+    bt.nsh_rep.resize(nrep);
+    bt.dsoff.resize(nrep + 1);
+    long long dso = 0;
+    for (int r = 0; r < nrep; r++) {
+        bt.nsh_rep[r] = bt.rep_sh0[r + 1] - bt.rep_sh0[r];
+        bt.maxsh = std::max(bt.maxsh, bt.nsh_rep[r]);
+        bt.dsoff[r] = dso;
+        dso += (long long)bt.nsh_rep[r] * bt.nsh_rep[r];
+    }
+    bt.dsoff[nrep] = dso;
+    int *d_sh0, *d_nshr;
+    long long* d_dsoff;
+    UPLOAD("rep_sh0", bt.rep_sh0, d_sh0);
+    UPLOAD("nsh_rep", bt.nsh_rep, d_nshr);
+    UPLOAD("dsoff", bt.dsoff, d_dsoff);
+    ENSURE("Dsh", dso, bt.Dsh);
+    ENSURE("cnt", 2 * 64, bt.cnt);
+    CK(cudaMemsetAsync(bt.cnt, 0, sizeof(unsigned long long) * 2 * 64, ctx->stream));
+    bt.R = Reps{d_nbf, d_moff, d_active, d_sh0, d_nshr, d_dsoff};
 
     // pair data, Schwarz factors (unsorted), then sort each group by Q
     int *d_pa, *d_pb, *d_npp;
@@ -515,6 +540,9 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
         UPLOAD("Q", Q, d_Q);
         bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q};
         launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
+        bt.npp.resize(npair);
+        if (npair) CK(cudaMemcpyAsync(bt.npp.data(), d_npp, sizeof(int) * npair, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
     }
     // quartet tiles: for bra pair i of class X and ket class Y <= X, the ket
     // pairs with Q_j >= tau / Q_i form a prefix of the sorted group.
@@ -524,6 +552,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     bt.nquart = 0;
     bt.nquart_rep.assign(nrep, 0);
     bt.vrr_flops = 0.0;
+    bt.eris = 0.0;
     for (int X = 0; X < 6; X++)
         for (int Y = 0; Y <= X; Y++) {
             const int cp = class_pair_index(X, Y);
@@ -547,10 +576,15 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
                     const long long nqi = kend - k0;
                     bt.nq_cp[cp] += nqi;
                     bt.nquart_rep[r] += nqi;
-                    const double npp_i = (double)bt.sh_nprim[bt.pa[i]] * bt.sh_nprim[bt.pb[i]];
+                    const double npp_i = (double)bt.npp[i];
                     double npp_k = 0.0;
-                    for (int k = k0; k < kend; k++) npp_k += (double)bt.sh_nprim[bt.pa[k]] * bt.sh_nprim[bt.pb[k]];
+                    for (int k = k0; k < kend; k++) npp_k += (double)bt.npp[k];
                     bt.vrr_flops += npp_i * npp_k * (double)class_vrr_flops(cp);
+                    {
+                        int la, lb, lc, ld;
+                        class_pair_ls(cp, &la, &lb, &lc, &ld);
+                        bt.eris += (double)nqi * nsph(la) * nsph(lb) * nsph(lc) * nsph(ld);
+                    }
                     for (int c = k0; c < kend; c += 128) tl.push_back(Tile{i, c, std::min(c + 128, kend), r});
                 }
             }
@@ -570,10 +604,11 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
 // SCF
 // ---------------------------------------------------------------------------
 struct Mats {
-    double *S, *H, *T, *V, *X, *F, *G, *D, *Fb, *M1, *M2, *Er, *C, *Cp, *W, *Ev, *work, *Cs;
+    double *S, *H, *T, *V, *X, *F, *G, *D, *Fb, *M1, *M2, *Er, *C, *Cp, *W, *Ev, *work, *Cs, *Cq;
     double *Fh, *Eh, *Bd, *coef;
     double *E, *emax, *enn;
-    int *slot, *count, *diis_on, *active, *fin;
+    double *Dp, *dD;
+    int *slot, *count, *diis_on, *active, *fin, *mode;
     RepMat* rm;
     int ldE;
 };
@@ -595,9 +630,13 @@ static int alloc_mats(pimd_ctx* ctx, Batch& bt, Mats& m, int hist)
     ENSURE("Er", mt, m.Er);
     ENSURE("C", mt, m.C);
     ENSURE("Cp", mt, m.Cp);
+    ENSURE("Cq", mt, m.Cq);
     ENSURE("W", mt, m.W);
     ENSURE("work", mt, m.work);
     ENSURE("Cs", mt, m.Cs);
+    ENSURE("Dp", mt, m.Dp);
+    ENSURE("dD", mt, m.dD);
+    ENSURE("mode", bt.nrep, m.mode);
     m.ldE = bt.maxN;
     ENSURE("Ev", (size_t)bt.nrep * m.ldE, m.Ev);
     const long long stride = (long long)bt.maxN * bt.maxN;
@@ -643,7 +682,7 @@ static int make_gemm(pimd_ctx* ctx, const char* name, const Batch& bt, const dou
 }
 
 struct ScfPlan {
-    GemmSet FD, FDS, XtE, XtEX, XtF, XtFX, XC, Dn, Wn;
+    GemmSet FD, FDS, XtE, XtEX, XtF, XtFX, QtF, FQ, QU, XC, Dn, Wn;
 };
 
 static int make_plan(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p)
@@ -655,7 +694,11 @@ static int make_plan(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p)
     if ((rc = make_gemm(ctx, "g_XtEX", bt, m.M1, 0, m.X, 0, m.M2, 1.0, false, p.XtEX))) return rc;
     if ((rc = make_gemm(ctx, "g_XtF", bt, m.X, 1, m.Fb, 0, m.M1, 1.0, false, p.XtF))) return rc;
     if ((rc = make_gemm(ctx, "g_XtFX", bt, m.M1, 0, m.X, 0, m.Cs, 1.0, false, p.XtFX))) return rc;
-    if ((rc = make_gemm(ctx, "g_XC", bt, m.X, 0, m.Cp, 0, m.C, 1.0, false, p.XC))) return rc;
+    if ((rc = make_gemm(ctx, "g_QtF", bt, m.Cq, 1, m.Cs, 0, m.M1, 1.0, false, p.QtF))) return rc;
+    if ((rc = make_gemm(ctx, "g_FQ", bt, m.M1, 0, m.Cq, 0, m.M2, 1.0, false, p.FQ))) return rc;
+    if ((rc = make_gemm(ctx, "g_QU", bt, m.Cq, 0, m.Cp, 0, m.M1, 1.0, false, p.QU))) return rc;
+    if ((rc = make_gemm(ctx, "g_XC", bt, m.X, 0, m.Cq, 0, m.C, 1.0, false, p.XC))) return rc;
+
     if ((rc = make_gemm(ctx, "g_Dn", bt, m.C, 0, m.C, 1, m.D, 2.0, true, p.Dn))) return rc;
     if ((rc = make_gemm(ctx, "g_Wn", bt, m.Cs, 0, m.C, 1, m.W, 2.0, true, p.Wn))) return rc;
     return PIMD_OK;
@@ -667,24 +710,33 @@ static void gemm(pimd_ctx* ctx, const GemmSet& g, const int* mask)
     ctx->stats.kernel_launches++;
 }
 
-// Fbar -> X^T Fbar X -> eigen -> C = X C', D = 2 C_occ C_occ^T (replicas in mask)
+// Fbar -> F' = X^T Fbar X, diagonalised in the basis of the previous
+// eigenvectors Q (F'' = Q^T F' Q is nearly diagonal, so the Jacobi sweeps start
+// close to convergence) -> Q <- Q U, C = X Q, D = 2 C_occ C_occ^T (replicas in mask)
 static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, const int* mask)
 {
     gemm(ctx, p.XtF, mask);
-    gemm(ctx, p.XtFX, mask);   // -> Cs (scratch)
-    launch_jacobi(m.rm, bt.nrep, m.Cs, m.Cp, m.Ev, m.ldE, m.work, mask, 1, ctx->stream);
+    gemm(ctx, p.XtFX, mask);   // F' -> Cs
+    gemm(ctx, p.QtF, mask);
+    gemm(ctx, p.FQ, mask);     // F'' -> M2
+    launch_jacobi(m.rm, bt.nrep, m.M2, m.Cp, m.Ev, m.ldE, m.work, mask, 1, ctx->stream);
+    gemm(ctx, p.QU, mask);     // Q U -> M1
+    launch_copy_mats(m.rm, bt.nrep, m.M1, m.Cq, mask, ctx->stream);
     gemm(ctx, p.XC, mask);
     gemm(ctx, p.Dn, mask);
-    ctx->stats.kernel_launches++;
+    ctx->stats.kernel_launches += 2;
 }
 
-static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau)
+// G' += G'(M) over all class pairs for the replicas in the active mask, with
+// the quartets screened by Q_ab Q_cd max|M block| >= tau
+static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, const double* M)
 {
-    CK(cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream));
+    launch_shell_bounds(bt.S, bt.R, bt.nrep, bt.maxsh, M, bt.Dsh, bt.R.active, ctx->stream);
+    ctx->stats.kernel_launches++;
     for (int cp = 0; cp < n_class_pairs(); cp++) {
         if (bt.tiles[cp].empty()) continue;
-        launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, m.G, ctx->boys, tau,
-                  ctx->stream);
+        launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), M, m.G, ctx->boys, tau, bt.Dsh,
+                  bt.cnt + 2 * cp, ctx->stream);
         ctx->stats.kernel_launches++;
     }
     return PIMD_OK;
@@ -746,22 +798,33 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     }
     int* d_mask;
     UPLOAD("mask_core", core, d_mask);
+    int* d_mc;
+    UPLOAD("mask_cache", use_cache, d_mc);
+    // starting eigenvector basis Q of the warm-started diagonalisation: the
+    // identity (the cached MOs are orthonormal for the previous geometry only,
+    // so they seed the density, not Q; Q stays orthogonal because it is only
+    // ever multiplied by Jacobi rotations)
+    launch_identity(m.rm, nrep, m.Cq, nullptr, ctx->stream);
     launch_copy_mats(m.rm, nrep, m.H, m.Fb, d_mask, ctx->stream);
     diag_density(ctx, bt, m, plan, d_mask);
-    {
-        int* d_mc;
-        UPLOAD("mask_cache", use_cache, d_mc);
-        gemm(ctx, plan.Dn, d_mc);
-    }
+    gemm(ctx, plan.Dn, d_mc);
     // SCF iterations
     std::vector<double> E(nrep), emax(nrep), Eprev(nrep, 0.0);
     std::vector<int> iters(nrep, 0), conv(nrep, 0);
     std::vector<double> fdE(nrep, 0.0), ferr(nrep, 0.0);
+    // build mode per replica: 2 full Fock build, 1 incremental (G' += G'(D - D_prev))
+    std::vector<int> mode(nrep, 2), since_full(nrep, 0);
+    const int full_every = 8;
     int nactive = nrep;
     for (int it = 1; it <= o->max_iter && nactive > 0; it++) {
+        for (int r = 0; r < nrep; r++) mode[r] = active[r] ? mode[r] : 0;
+        int* d_mode;
+        UPLOAD("mode", mode, d_mode);
         CK(cudaEventRecord(ctx->ev[2], ctx->stream));
-        if ((rc = fock_build(ctx, bt, m, o->schwarz_tau))) return rc;
+        launch_delta_density(m.rm, nrep, m.D, m.Dp, m.dD, m.G, d_mode, ctx->stream);
+        if ((rc = fock_build(ctx, bt, m, o->schwarz_tau, m.dD))) return rc;
         CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+        ctx->stats.kernel_launches++;
         ctx->stats.fock_builds++;
         launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, m.active, ctx->stream);
         launch_energy(m.rm, nrep, m.D, m.H, m.F, m.enn, m.E, m.active, ctx->stream);
@@ -789,7 +852,9 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             iters[r] = it;
             fdE[r] = it > 1 ? fabs(E[r] - Eprev[r]) : INFINITY;
             ferr[r] = emax[r];
-            if (it > 1 && fdE[r] < o->conv_energy && emax[r] < o->conv_error) {
+            const bool met = it > 1 && fdE[r] < o->conv_energy && emax[r] < o->conv_error;
+            // convergence is only accepted on a full (non-incremental) build
+            if (met && mode[r] == 2) {
                 fin[r] = 1;
                 conv[r] = 1;
                 anyfin = true;
@@ -797,6 +862,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
                 fin[r] = 1;
                 anyfin = true;
             }
+            since_full[r] = mode[r] == 2 ? 1 : since_full[r] + 1;
+            mode[r] = (met || since_full[r] >= full_every) ? 2 : 1;
             Eprev[r] = E[r];
         }
         if (anyfin) {
@@ -848,6 +915,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             launch_vnn(bt.At, natot, d_ar, d_dummy, d_grad, ctx->stream);
         }
         CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+        launch_shell_bounds(bt.S, bt.R, nrep, bt.maxsh, m.D, bt.Dsh, nullptr, ctx->stream);
         const int grid_blocks = ctx->nsm * 4;
         size_t scr = 0;
         for (int cp = 0; cp < n_class_pairs(); cp++) scr = std::max(scr, grad2e_scratch_bytes(cp, grid_blocks * 128));
@@ -856,7 +924,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         for (int cp = 0; cp < n_class_pairs(); cp++) {
             if (bt.tiles[cp].empty()) continue;
             launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_grad, ctx->boys,
-                          o->schwarz_tau, d_scr, grid_blocks, ctx->stream);
+                          o->schwarz_tau * 1e-2, d_scr, grid_blocks, bt.Dsh, ctx->stream);
             ctx->stats.kernel_launches++;
         }
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
@@ -893,7 +961,21 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         }
     }
     ctx->stats.nquartets_total = bt.nquart;
-    ctx->stats.eri_flops_per_build = bt.vrr_flops;
+    {
+        // executed work of all Fock builds of the call, from the device counters
+        std::vector<unsigned long long> cnt(2 * 64);
+        CK(cudaMemcpy(cnt.data(), bt.cnt, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
+        double fl = 0.0, er = 0.0;
+        for (int cp = 0; cp < n_class_pairs(); cp++) {
+            int la, lb, lc, ld;
+            class_pair_ls(cp, &la, &lb, &lc, &ld);
+            fl += (double)cnt[2 * cp + 1] * class_vrr_flops(cp);
+            er += (double)cnt[2 * cp] * nsph(la) * nsph(lb) * nsph(lc) * nsph(ld);
+        }
+        const int nb = std::max(1, ctx->stats.fock_builds);
+        ctx->stats.eri_flops_per_build = fl / nb;
+        ctx->stats.eris_per_build = er / nb;
+    }
     bool allconv = true;
     for (int r = 0; r < nrep; r++) {
         if (info) {
@@ -1020,7 +1102,8 @@ extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
     UPLOAD("active", active, m.active);
     bt.R.active = m.active;
     CK(cudaMemcpyAsync(m.D, D_dev, sizeof(double) * bt.mtot, cudaMemcpyDeviceToDevice, ctx->stream));
-    if ((rc = fock_build(ctx, bt, m, schwarz_tau))) return rc;
+    CK(cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream));
+    if ((rc = fock_build(ctx, bt, m, schwarz_tau, m.D))) return rc;
     // G_out = G' + G'^T
     CK(cudaMemsetAsync(m.H, 0, sizeof(double) * bt.mtot, ctx->stream));
     launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, nullptr, ctx->stream);

@@ -32,7 +32,8 @@ class PimdInfo(ctypes.Structure):
 class PimdStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("fock_builds", ctypes.c_int),
                 ("ms_fock", ctypes.c_double), ("ms_grad2e", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("nquartets_total", ctypes.c_longlong), ("eri_flops_per_build", ctypes.c_double)]
+                ("nquartets_total", ctypes.c_longlong), ("eri_flops_per_build", ctypes.c_double),
+                ("eris_per_build", ctypes.c_double)]
 
 
 class PimdError(RuntimeError):

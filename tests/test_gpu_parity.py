@@ -152,3 +152,28 @@ def test_ragged_images(ctx, spd):
         assert abs(E[k] - E0) < E_TOL, (k, E[k] - E0)
         assert np.abs(G[off:off + len(z)] - G0).max() < G_TOL
         off += len(z)
+
+
+def test_mo_reuse_guess_matches_core_guess(ctx):
+    """Sec. 2: each replica's MOs are reused as the next step's guess; the
+    converged result must not depend on the guess."""
+    reps, kind = inputs.workload("water2_min_4beads")
+    bas = inputs.basis_set(kind)
+    B = native.Basis(bas)
+    seq = inputs.markov_steps(reps, 3, seed=5)
+    ctx.clear_guess()
+    res = {}
+    for gs in (1, 0):
+        ctx.clear_guess()
+        for s in range(3):
+            Z, X = seq[s].stacked()
+            E, G, info, rc = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=gs))
+            assert rc == 0
+            res[(gs, s)] = (E, G, [i["iterations"] for i in info])
+    for s in range(3):
+        E1, G1, it1 = res[(1, s)]
+        E0, G0, it0 = res[(0, s)]
+        assert np.abs(E1 - E0).max() < 1e-9
+        assert np.abs(G1 - G0).max() < 1e-7
+        if s > 0:
+            assert np.mean(it1) <= np.mean(it0)
