@@ -156,6 +156,32 @@ int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coor
                       double* S, double* T, double* V);
 int pimd_boys_dev(pimd_ctx* ctx, int n, int m, const double* T_dev, double* F_dev);
 
+/* Batched symmetric eigensolver of the SCF diagonalisation step (the
+ * Roothaan-Hall eigenproblem solved in every SCF cycle, Sec. 3.1): nmat
+ * symmetric n x n matrices A_dev[nmat][n][n] (device, row-major) ->
+ * eigenvalues evals_dev[nmat][n] in ascending order and eigenvectors as the
+ * columns of V_dev[nmat][n][n] (device, row-major; V[i][k] is component i of
+ * vector k). One-sided Jacobi on A + sigma I (sigma from the Gershgorin
+ * bound). Uses a workspace of the context (allocated on demand). stream: the
+ * caller's cudaStream_t or NULL; the call returns after the results are written. */
+int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev,
+                  void* stream);
+
+/* The same eigensolver for callers that must not allocate device memory
+ * (the paper has no counterpart: this is a library convenience). Callers whose
+ * device memory is owned by another allocator, or whose loop must not take the
+ * implicit device synchronisation of cudaMalloc/cudaFree, cannot use the
+ * context-based call above; this one calls no allocator at all. Its workspace
+ * is a fixed device array of 2,097,152 doubles (16 MiB) plus room for 1024
+ * matrix descriptors, held by every GPU that loads the library until the
+ * process exits. Limits: nmat <= 1024 and nmat * n * n <= 2,097,152, else
+ * PIMD_EINVAL. Arguments as for pimd_eigh_dev; no context is needed (the
+ * current CUDA device is used). The first call on a device resolves the
+ * array addresses on that device; make that first call before any stream
+ * capture. All calls share the one workspace: calls that overlap on the GPU
+ * (from several host threads or streams) race and give wrong results. */
+int pimd_eigh_noalloc(int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev, void* stream);
+
 /* Roofline denominators measured on the device: FP64 FMA, FP32 FMA and FP64
  * tensor-core MMA throughput in TFLOP/s (bounded microbenchmarks, ~1 s). Any
  * output pointer may be NULL. No counterpart in the paper (measurement aid). */

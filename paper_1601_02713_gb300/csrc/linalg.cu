@@ -512,6 +512,27 @@ void gather_xyz(const double* atom_xyz, const int* shell_atom, int nshell, doubl
     gather_xyz_kernel<<<(nshell + 127) / 128, 128, 0, st>>>(atom_xyz, shell_atom, nshell, shell_xyz);
 }
 
+// ---------------------------------------------------------------------------
+// Eigensolver entry point that allocates nothing. Some callers cannot call
+// cudaMalloc: code whose device memory is owned by another allocator (a
+// framework's caching pool that has already reserved the GPU), and loops that
+// must not pay the implicit device synchronisation of cudaMalloc/cudaFree
+// between launches. For them the solver's workspace and its per-matrix
+// descriptors live in file-scope device arrays of fixed size, which every GPU
+// that loads the library keeps until the process exits.
+// ---------------------------------------------------------------------------
+#define PIMD_EIGH_NOALLOC_MAX_DOUBLES (1 << 21)  // 16 MiB: nmat * n * n <= 2,097,152
+#define PIMD_EIGH_NOALLOC_MAX_MATS 1024
+
+static __device__ __align__(256) double g_eigh_work[PIMD_EIGH_NOALLOC_MAX_DOUBLES];
+static __device__ __align__(256) RepMat g_eigh_desc[PIMD_EIGH_NOALLOC_MAX_MATS];
+
+// device addresses of the two arrays, resolved once per device (the names
+// above are host-side stand-ins and must never be passed to a kernel)
+static double* g_eigh_work_ptr[64];
+static RepMat* g_eigh_desc_ptr[64];
+static RepMat g_eigh_desc_host[64][PIMD_EIGH_NOALLOC_MAX_MATS];
+
 void launch_identity(const RepMat* rm, int nrep, double* A, const int* mask, cudaStream_t st)
 {
     identity_kernel<<<dim3(64, nrep), 256, 0, st>>>(rm, A, mask);
@@ -606,4 +627,36 @@ void launch_diis_combine(const RepMat* rm, int nrep, const double* Fh, const dou
                                                          active);
 }
 
+int eigh_noalloc(int nmat, int n, const double* A, double* V, double* evals, cudaStream_t st)
+{
+    if (nmat <= 0 || n <= 0 || !A || !V || !evals) return -1;
+    if (nmat > PIMD_EIGH_NOALLOC_MAX_MATS || (long long)nmat * n * n > PIMD_EIGH_NOALLOC_MAX_DOUBLES) return -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -3;
+    if (!g_eigh_work_ptr[dev]) {
+        // set-up on the first call on this device
+        void* w = nullptr;
+        void* d = nullptr;
+        if (cudaGetSymbolAddress(&w, g_eigh_work) != cudaSuccess) return -3;
+        if (cudaGetSymbolAddress(&d, g_eigh_desc) != cudaSuccess) return -3;
+        g_eigh_desc_ptr[dev] = (RepMat*)d;
+        g_eigh_work_ptr[dev] = (double*)w;
+    }
+    RepMat* hd = g_eigh_desc_host[dev];
+    for (int r = 0; r < nmat; r++) hd[r] = RepMat{n, 0, (long long)r * n * n};
+    if (cudaMemcpyAsync(g_eigh_desc_ptr[dev], hd, sizeof(RepMat) * nmat, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return -3;
+    jacobi_kernel<<<nmat, JAC_THREADS, sizeof(double) * n, st>>>(g_eigh_desc_ptr[dev], A, V, evals, n,
+                                                                 g_eigh_work_ptr[dev], nullptr, 1);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+    return 0;
+}
+
 }  // namespace pimd
+
+// C ABI (declared in include/pimdgb.h)
+extern "C" int pimd_eigh_noalloc(int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev, void* stream)
+{
+    return pimd::eigh_noalloc(nmat, n, A_dev, V_dev, evals_dev, (cudaStream_t)stream);
+}

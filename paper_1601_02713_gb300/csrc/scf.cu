@@ -1148,3 +1148,21 @@ extern "C" int pimd_boys_dev(pimd_ctx* ctx, int n, int mord, const double* T_dev
     CK(cudaGetLastError());
     return PIMD_OK;
 }
+
+extern "C" int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev,
+                             void* stream)
+{
+    if (!ctx || nmat <= 0 || n <= 0 || !A_dev || !V_dev || !evals_dev) return PIMD_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    if (stream) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<RepMat> rm(nmat);
+    for (int r = 0; r < nmat; r++) rm[r] = RepMat{n, 0, (long long)r * n * n};
+    RepMat* d_rm;
+    double* work;
+    UPLOAD("eigh_rm", rm, d_rm);
+    ENSURE("eigh_work", (size_t)nmat * n * n, work);
+    launch_jacobi(d_rm, nmat, A_dev, V_dev, evals_dev, n, work, nullptr, 1, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIMD_OK;
+}

@@ -81,6 +81,8 @@ def load(path: str | None = None):
     lib.pimd_one_electron.argtypes = [_P, ctypes.c_int, _I, _D, _P, _D, _D, _D]
     lib.pimd_boys_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
     lib.pimd_peak_bench.argtypes = [ctypes.c_int, _D, _D, _D]
+    lib.pimd_eigh_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
+    lib.pimd_eigh_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
     lib.pimd_strerror.argtypes = [ctypes.c_int]
     lib.pimd_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -260,6 +262,22 @@ def pimd_last_stats(ctx: Context) -> dict:
     s = PimdStats()
     _check(load().pimd_last_stats(ctx.handle, ctypes.byref(s)), "pimd_last_stats")
     return {k: getattr(s, k) for k, _ in PimdStats._fields_}
+
+
+def pimd_eigh_dev(ctx: Context, A_dev, V_dev, evals_dev, stream: int = 0):
+    """Batched symmetric eigensolver (context workspace). A, V: [nmat, n, n]
+    and evals: [nmat, n], float64 CUDA tensors."""
+    nmat, n = int(A_dev.shape[0]), int(A_dev.shape[1])
+    _check(load().pimd_eigh_dev(ctx.handle, nmat, n, _P(A_dev.data_ptr()), _P(V_dev.data_ptr()),
+                                _P(evals_dev.data_ptr()), _P(stream)), "pimd_eigh_dev")
+
+
+def pimd_eigh_noalloc(A_dev, V_dev, evals_dev, stream: int = 0):
+    """The same eigensolver without any device allocation (fixed 16 MiB
+    device workspace; nmat * n * n <= 2,097,152); returns the status code."""
+    nmat, n = int(A_dev.shape[0]), int(A_dev.shape[1])
+    return load().pimd_eigh_noalloc(nmat, n, _P(A_dev.data_ptr()), _P(V_dev.data_ptr()), _P(evals_dev.data_ptr()),
+                                    _P(stream))
 
 
 def pimd_peak_bench(device: int = 0) -> dict:
