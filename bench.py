@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water8_spd_32beads")
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-quartets", type=int, default=100000)
     ap.add_argument("--cpu-sample-deriv", type=int, default=8000)
+    ap.add_argument("--fp32-tau", type=float, default=0.0,
+                    help="mixed precision: quartets with Q_ab Q_cd max|dD| below this run in FP32 (0: all FP64)")
     return ap.parse_args()
 
 
@@ -197,7 +199,7 @@ def main():
     natom = len(Z)
     ctx = native.Context(local)
     basis = native.Basis(inputs.basis_set(kind))
-    opts = native.scf_opts(guess=1)
+    opts = native.scf_opts(guess=1, fp32_tau=args.fp32_tau)
     dev = torch.device("cuda", local)
     X = [torch.tensor(s.stacked()[1], dtype=torch.float64, device=dev) for s in seq]
     E = torch.empty(nrep, dtype=torch.float64, device=dev)
@@ -270,13 +272,16 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if args.fp32_tau == 0 else "f64+f32", "data": "synthetic",
             "config": {"workload": args.workload, "beads_per_rank": nrep, "atoms": natom,
                        "basis": f"{kind} (even-tempered, {native.Basis(inputs.basis_set(kind)).nbf(Z)} functions)",
                        "scf": "|dE|<1e-10, max|FDS-SDF|<1e-8, DIIS(8), MO reuse between steps",
-                       "schwarz_tau": 1e-12, "l2": "flushed before every timed step (512 MB write)",
+                       "schwarz_tau": 1e-12, "fp32_tau": args.fp32_tau,
+                       "l2": "flushed before every timed step (512 MB write)",
                        "parallelism": f"replicas{world}"},
             "geri_per_s": geri,
+            "fp32_quartet_fraction": (sum(s["quartets_fp32"] for s in stats)
+                                      / max(1, sum(s["quartets_fp32"] + s["quartets_fp64"] for s in stats))),
             "fock_builds_per_step": builds / K,
             "scf_iterations_mean": statistics.mean(iters),
             "roofline": {"kernel": "jk_kernel (one Fock build = all quartet classes)", "bound": "alu",

@@ -17,6 +17,7 @@
  *   units: coordinates in bohr, energies in hartree, gradients dE/dR in
  *          hartree/bohr (the force is minus the gradient);
  *   charge 0, closed shell (the electron count sum(Z) must be even);
+ *   at most 768 basis functions per replica;
  *   all array arguments of the host entry points are caller-owned HOST memory,
  *   read before the call returns; outputs are written before it returns
  *   (the call synchronises its stream);
@@ -56,7 +57,9 @@ typedef struct {
     int max_iter;         /* 64 */
     int diis_size;        /* 8 (Pulay subspace, 2..8) */
     double schwarz_tau;   /* 1e-12: quartets with Q_ab Q_cd below it are skipped (Sec. 3.1) */
-    double fp32_tau;      /* 0: all quartets in FP64 */
+    double fp32_tau;      /* 0: all quartets in FP64; > schwarz_tau: quartets whose bound
+                             Q_ab Q_cd max|D block| is below it (D: the density increment of an
+                             incremental build) are evaluated in FP32 and accumulated in FP64 */
     int guess;            /* 0 core Hamiltonian, 1 previous MOs of the same replica index (Sec. 2:
                              MOs of each replica reused as the next step's guess), falls back to 0 */
     int deterministic;    /* reserved, 0 */
@@ -142,6 +145,9 @@ typedef struct {
                                     averaged over the call's builds (generated recursion + per-primitive
                                     set-up and Boys, counted from the generated code), all replicas */
     double eris_per_build;       /* executed unique contracted basis-function ERIs per Fock build (average) */
+    double eri_flops32_per_build;  /* the same operations count for the FP32 quartets (mixed mode) */
+    long long quartets_fp64;     /* executed shell quartets of all Fock builds of the call, FP64 */
+    long long quartets_fp32;     /* ... and FP32 (fp32_tau > 0) */
 } pimd_stats;
 int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
 
@@ -162,8 +168,9 @@ int pimd_boys_dev(pimd_ctx* ctx, int n, int m, const double* T_dev, double* F_de
  * eigenvalues evals_dev[nmat][n] in ascending order and eigenvectors as the
  * columns of V_dev[nmat][n][n] (device, row-major; V[i][k] is component i of
  * vector k). One-sided Jacobi on A + sigma I (sigma from the Gershgorin
- * bound). Uses a workspace of the context (allocated on demand). stream: the
- * caller's cudaStream_t or NULL; the call returns after the results are written. */
+ * bound), n <= 768. Uses a workspace of the context (allocated on demand).
+ * stream: the caller's cudaStream_t or NULL; the call returns after the results
+ * are written. */
 int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev,
                   void* stream);
 
@@ -174,7 +181,7 @@ int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V
  * context-based call above; this one calls no allocator at all. Its workspace
  * is a fixed device array of 2,097,152 doubles (16 MiB) plus room for 1024
  * matrix descriptors, held by every GPU that loads the library until the
- * process exits. Limits: nmat <= 1024 and nmat * n * n <= 2,097,152, else
+ * process exits. Limits: n <= 768, nmat <= 1024 and nmat * n * n <= 2,097,152, else
  * PIMD_EINVAL. Arguments as for pimd_eigh_dev; no context is needed (the
  * current CUDA device is used). The first call on a device resolves the
  * array addresses on that device; make that first call before any stream

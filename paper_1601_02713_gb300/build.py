@@ -56,6 +56,49 @@ def _write(path, text):
         fh.write(text)
 
 
+def _coop_upload_code(nm, grad, g):
+    """C++ lines defining coop_tape_<nm>(CoopTape&, int& warps, size_t& smem):
+    uploads the class's tape once per device and sizes the launch."""
+    pre = f"coop{'g' if grad else 'e'}_{nm}"
+    st = f"Coop{'G' if grad else 'E'}_{nm}"
+    c = [cl for cl in g.classes() if g.cls_name(cl) == nm][0]
+    hr = g.grad_hrrs(c) if grad else [("E", c, "acc")]
+    la, lb, lc, ld = c
+    nc4 = g.ncart(la) * g.ncart(lb) * g.ncart(lc) * g.ncart(ld)
+    kernel = (f"grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}>" if grad else f"jk_coop_kernel<{la}, {lb}, {lc}, {ld}>")
+    lines = ["static CoopTape g_coop[64];", "static bool g_coop_up[64];",
+             "template <typename T> static const T* coop_copy(const T* h, size_t n)",
+             "{", "    T* d = nullptr;", "    cudaMalloc(&d, n * sizeof(T));",
+             "    cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice);", "    return d;", "}",
+             f"static void coop_tape_{nm}(CoopTape& t, int& W, size_t& bytes)", "{",
+             "    int dev = 0;", "    cudaGetDevice(&dev);",
+             f"    const int per = coop_warp_doubles({st}::NACC, {st}::NWORK, {st}::L, {nc4});",
+             "    W = (int)(220 * 1024 / (per * sizeof(double)));",
+             "    W = W < 1 ? 1 : (W > 4 ? 4 : W);",
+             "    bytes = (size_t)W * per * sizeof(double);",
+             "    if (dev >= 0 && dev < 64 && !g_coop_up[dev]) {",
+             "        CoopTape c{};",
+             f"        c.vrr = coop_copy({pre}_vrr, sizeof({pre}_vrr) / sizeof(int));",
+             f"        c.vrr_lv = coop_copy({pre}_vrr_lv, sizeof({pre}_vrr_lv) / sizeof(int));",
+             f"        c.acc = coop_copy({pre}_acc, sizeof({pre}_acc) / sizeof(int));",
+             f"        c.nvlev = {st}::NVLEV;", f"        c.naccop = {st}::NACCOP;",
+             f"        c.nhrr = {len(hr)};",
+             f"        c.L = {st}::L;", f"        c.NACC = {st}::NACC;", f"        c.F0 = {st}::F0;",
+             f"        c.NWORK = {st}::NWORK;"]
+    for k, (hname, cls_, src) in enumerate(hr):
+        pos = {"A": 0, "B": 1, "C": 2, "E": 0}[hname[0]]
+        up = 1 if hname.endswith("p") or hname == "E" else 0
+        lines += [f"        c.hrr[{k}] = coop_copy({pre}_hrr{hname}, sizeof({pre}_hrr{hname}) / sizeof(int));",
+                  f"        c.hrr_lv[{k}] = coop_copy({pre}_hrr{hname}_lv, sizeof({pre}_hrr{hname}_lv) / sizeof(int));",
+                  f"        c.nhlev[{k}] = (int)(sizeof({pre}_hrr{hname}_lv) / sizeof(int)) - 1;",
+                  f"        c.out[{k}] = coop_copy({pre}_out{hname}, sizeof({pre}_out{hname}) / sizeof(int));",
+                  f"        c.hpos[{k}] = {pos};", f"        c.hup[{k}] = {up};"]
+    lines += ["        g_coop[dev] = c;", "        g_coop_up[dev] = true;",
+              f"        cudaFuncSetAttribute({kernel}, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);",
+              "    }", "    t = g_coop[dev];", "}"]
+    return lines
+
+
 def generate_sources():
     """Generated headers + per-class translation units + dispatch. Returns the
     list of generated .cu files."""
@@ -63,20 +106,41 @@ def generate_sources():
     os.makedirs(GEN, exist_ok=True)
     stats = g.generate(GEN)
     heavy = {s[0]: s[6] for s in stats}
+    coop_e = {s[0]: s[7] for s in stats}
     classes = g.classes()
     names = [g.cls_name(c) for c in classes]
     tus = []
     for c, nm in zip(classes, names):
         la, lb, lc, ld = c
         same = (la, lb) == (lc, ld)
-        e = ['#include "eri_kernels.cuh"', '#include "internal.h"', f'#include "eri_{nm}.cuh"',
-             "namespace pimd {",
-             f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-             "                     const double* D, double* G, const double* boys, double tau, const double* Dsh,",
-             "                     unsigned long long* cnt, cudaStream_t st)",
-             "{",
-             f"    if (ntiles > 0) jk_kernel<Cls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, G, boys, tau, Dsh, cnt);",
-             "}"]
+        e = ['#include "coop_kernels.cuh"', '#include "internal.h"', f'#include "eri_{nm}.cuh"']
+        if coop_e[nm]:
+            e.append(f'#include "coope_{nm}.cuh"')
+        e.append("namespace pimd {")
+        if coop_e[nm]:
+            e += _coop_upload_code(nm, False, g)
+            e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
+                  "                     const double* D, const float*, double* G, const double* boys, const float*,",
+                  "                     double tau, double, const double* Dsh, unsigned long long* cnt, cudaStream_t st)",
+                  "{",
+                  f"    CoopTape t; int W; size_t bytes;",
+                  f"    coop_tape_{nm}(t, W, bytes);",
+                  f"    if (ntiles > 0) jk_coop_kernel<{la}, {lb}, {lc}, {ld}><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles, D,",
+                  "        G, boys, tau, Dsh, cnt, t);",
+                  "}"]
+        else:
+            e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
+                  "                     const double* D, const float* Df, double* G, const double* boys,",
+                  "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
+                  "                     unsigned long long* cnt, cudaStream_t st)",
+                  "{",
+                  "    if (ntiles <= 0) return;",
+                  "    const double split = fp32_tau > tau ? fp32_tau : tau;",
+                  f"    jk_kernel<Cls_{nm}, double><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt);",
+                  "    if (fp32_tau > tau)",
+                  f"        jk_kernel<Cls_{nm}, float><<<ntiles, 128, 0, st>>>(P, S, R, tiles, Df, G, boysf, tau, fp32_tau, Dsh,",
+                  "                                                        cnt + 2);",
+                  "}"]
         if same:
             e += [f"void launch_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
                   "                          const double* boys, double* Q, cudaStream_t st)",
@@ -87,9 +151,9 @@ def generate_sources():
         p = os.path.join(GEN, f"tu_eri_{nm}.cu")
         _write(p, "\n".join(e))
         tus.append(p)
-        gl = ['#include "grad_kernels.cuh"', '#include "internal.h"', f'#include "grad_{nm}.cuh"']
+        gl = ['#include "coop_kernels.cuh"', '#include "internal.h"', f'#include "grad_{nm}.cuh"']
         if heavy[nm]:
-            gl.append(f'#include "grad_tape_{nm}.cuh"')
+            gl.append(f'#include "coopg_{nm}.cuh"')
         gl.append("namespace pimd {")
         if not heavy[nm]:
             gl += [f"void grad2e_upload_{nm}() {{}}",
@@ -101,45 +165,17 @@ def generate_sources():
                    f"    if (ntiles > 0) grad2e_kernel<GCls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boys, tau, Dsh);",
                    "}"]
         else:
-            gl += ["static TapeDev g_tape[64];",
-                   "static bool g_up[64];",
-                   "template <typename T> static const T* dev_copy(const T* h, size_t n)",
-                   "{",
-                   "    T* d = nullptr;",
-                   "    cudaMalloc(&d, n * sizeof(T));",
-                   "    cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice);",
-                   "    return d;",
-                   "}",
-                   f"void grad2e_upload_{nm}()",
-                   "{",
-                   "    int dev = 0;",
-                   "    cudaGetDevice(&dev);",
-                   "    if (dev < 0 || dev >= 64 || g_up[dev]) return;",
-                   "    TapeDev t;",
-                   "    t.vrr = dev_copy(tape_vrr, sizeof(tape_vrr) / sizeof(int));",
-                   "    t.acc = dev_copy(tape_acc, sizeof(tape_acc) / sizeof(int));",
-                   "    t.hrr = dev_copy(tape_hrr, sizeof(tape_hrr) / sizeof(int));",
-                   "    const int* outs[6] = {tape_outAp, tape_outBp, tape_outCp, tape_outAm, tape_outBm, tape_outCm};",
-                   "    const size_t nout[6] = {sizeof(tape_outAp), sizeof(tape_outBp), sizeof(tape_outCp),",
-                   "                            sizeof(tape_outAm), sizeof(tape_outBm), sizeof(tape_outCm)};",
-                   "    for (int k = 0; k < 6; k++) t.out[k] = dev_copy(outs[k], nout[k] / sizeof(int));",
-                   f"    t.nvrr = Tape_{nm}::NVRR;",
-                   f"    t.nacc = Tape_{nm}::NACC;",
-                   f"    t.nhrr = Tape_{nm}::NHRR;",
-                   f"    t.nslot = Tape_{nm}::NSLOT;",
-                   "    g_tape[dev] = t;",
-                   "    g_up[dev] = true;",
-                   "}",
-                   f"size_t grad2e_scratch_{nm}(int threads) {{ return (size_t)Tape_{nm}::NSLOT * threads * sizeof(double); }}",
+            gl += _coop_upload_code(nm, True, g)
+            gl += [f"void grad2e_upload_{nm}() {{ CoopTape t; int W; size_t b; coop_tape_{nm}(t, W, b); }}",
+                   f"size_t grad2e_scratch_{nm}(int) {{ return 0; }}",
                    f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                   "                        const double* D, double* grad, const double* boys, double tau,",
-                   "                        double* scratch, int grid_blocks, const double* Dsh, cudaStream_t st)",
+                   "                        const double* D, double* grad, const double* boys, double tau, double*, int,",
+                   "                        const double* Dsh, cudaStream_t st)",
                    "{",
-                   f"    grad2e_upload_{nm}();",
-                   "    int dev = 0;",
-                   "    cudaGetDevice(&dev);",
-                   f"    if (ntiles > 0) grad2e_tape_kernel<GCls_{nm}><<<grid_blocks, 128, 0, st>>>(P, S, R, tiles, ntiles, D,",
-                   "        grad, boys, tau, g_tape[dev], scratch, Dsh);",
+                   "    CoopTape t; int W; size_t bytes;",
+                   f"    coop_tape_{nm}(t, W, bytes);",
+                   f"    if (ntiles > 0) grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles,",
+                   "        D, grad, boys, tau, Dsh, t);",
                    "}"]
         gl.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_grad_{nm}.cu")
@@ -147,8 +183,8 @@ def generate_sources():
         tus.append(p)
     # dispatch
     d = ['#include "internal.h"', "namespace pimd {"]
-    sig_jk = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-              "double, const double*, unsigned long long*, cudaStream_t")
+    sig_jk = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, const float*, double*, "
+              "const double*, const float*, double, double, const double*, unsigned long long*, cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
              "double, double*, int, const double*, cudaStream_t")
@@ -168,19 +204,20 @@ def generate_sources():
     flops = {s[0]: s[2] for s in stats}
     d.append("long long class_vrr_flops(int cp)")
     d.append("{")
-    # per primitive quartet: the generated recursion's operations plus the
-    # set-up of prim_quartet (41), the Boys Taylor step and recursion (19 + 2L)
-    # and the prefactor scaling (L + 1)
-    d.append("    static const long long t[] = {" + ", ".join(str(flops[nm] + 61 + 3 * sum(c))
+    # per primitive quartet: the generated recursion's operations (an FMA
+    # counts 2) plus the set-up of prim_quartet (25) and the Boys function
+    # (17 for the Taylor step and prefactor; for L > 0 also 16 for e^{-T} and
+    # 3 per order of the downward recursion)
+    d.append("    static const long long t[] = {" + ", ".join(str(flops[nm] + 42 + (16 + 3 * sum(c) if sum(c) else 0))
                                                         for c, nm in zip(classes, names)) + "};")
     d.append("    return t[cp];")
     d.append("}")
     d.append(f"typedef void (*JkFn)({sig_jk});")
     d.append("static const JkFn jk_tab[] = {" + ", ".join(f"launch_jk_{nm}" for nm in names) + "};")
     d.append("void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
-             "const double* D, double* G, const double* boys, double tau, const double* Dsh, unsigned long long* cnt, "
-             "cudaStream_t st)")
-    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, G, boys, tau, Dsh, cnt, st); }")
+             "const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau, "
+             "double fp32_tau, const double* Dsh, unsigned long long* cnt, cudaStream_t st)")
+    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, st); }")
     same = [nm for c, nm in zip(classes, names) if (c[0], c[1]) == (c[2], c[3])]
     d.append(f"typedef void (*SwFn)({sig_sw});")
     d.append("static const SwFn sw_tab[] = {" + ", ".join(f"launch_schwarz_{nm}" for nm in same) + "};")

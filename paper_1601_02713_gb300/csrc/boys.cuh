@@ -1,15 +1,19 @@
-// Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt on the device.
+// Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt on the device, scaled
+// by a prefactor theta (the Obara-Saika [00|00]^(m) = theta F_m(T)).
 //
 // T < BOYS_TMAX: the top order F_L is a 7th-order Taylor expansion about the
-// nearest grid point T_k = k / BOYS_GRID of a table of F_m(T_k),
-//   F_L(T) = sum_j F_{L+j}(T_k) (T_k - T)^j / j!      (d F_m / dT = -F_{m+1}),
-// and the lower orders follow from the downward recursion
+// nearest grid point T_k = k / BOYS_GRID,
+//   F_L(T) = sum_j F_{L+j}(T_k) (T_k - T)^j / j!      (dF_m/dT = -F_{m+1}),
+// read from a table that stores F_{m+j}(T_k) / j! so that each term is one
+// fused multiply-add; e^{-T} = e^{-T_k} e^{T_k - T} with the exponential
+// series to 7th order (|T_k - T| <= 1/32, so the truncation is below 1e-16
+// relative); the lower orders follow from the downward recursion
 //   F_m(T) = (2 T F_{m+1}(T) + e^{-T}) / (2m + 1),
-// which is stable for all T. T >= BOYS_TMAX: F_0 = (1/2) sqrt(pi / T) (erf of
-// sqrt(T) is 1 in double precision there) and the upward recursion
+// stable for all T. T >= BOYS_TMAX: F_0 = (1/2) sqrt(pi / T) (erf of sqrt(T)
+// is 1 in double precision there) and the upward recursion
 //   F_{m+1} = ((2m + 1) F_m - e^{-T}) / (2T),
 // stable because 2T > 2m + 1 for every order used here.
-// The table is filled on the host by `boys_fill_table` (series in long double).
+// The tables are filled on the host by `boys_fill_table` (series in long double).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -17,68 +21,123 @@
 #define BOYS_TMAX 40.0
 #define BOYS_NT (40 * BOYS_GRID + 1)
 #define BOYS_MMAX 12          // highest order any kernel asks for
-#define BOYS_NTAYLOR 8        // Taylor terms (FP64)
-#define BOYS_NM (BOYS_MMAX + BOYS_NTAYLOR)   // table orders per grid point
+#define BOYS_NTAYLOR 8        // Taylor terms
+#define BOYS_MT (BOYS_MMAX + 1)
+// table layout: [BOYS_NT][BOYS_MT][BOYS_NTAYLOR] F_{m+j}(T_k)/j!, then [BOYS_NT] e^{-T_k}
+#define BOYS_TAB_DOUBLES (BOYS_NT * BOYS_MT * BOYS_NTAYLOR + BOYS_NT)
+
+// FP32 table for the mixed-precision quartets: [BOYS_NT][BOYS_MT][4]
+// F_{m+j}(T_k)/j! then [BOYS_NT] e^{-T_k} (4 Taylor terms: truncation below
+// 5e-8 relative, under single-precision rounding of the recursion)
+#define BOYS_NTAYLOR_F 4
+#define BOYS_TAB_FLOATS (BOYS_NT * BOYS_MT * BOYS_NTAYLOR_F + BOYS_NT)
 
 namespace pimd {
 
-// Host: fill tab[k * BOYS_NM + m] = F_m(k / BOYS_GRID).
+// Host: fill the table (BOYS_TAB_DOUBLES values).
 void boys_fill_table(double* tab);
 
+__device__ __forceinline__ double exp_poly(double x)
+{
+    // e^x = sum_j x^j / j!, j <= 7
+    double e = 1.0 / 5040.0;
+    e = fma(e, x, 1.0 / 720.0);
+    e = fma(e, x, 1.0 / 120.0);
+    e = fma(e, x, 1.0 / 24.0);
+    e = fma(e, x, 1.0 / 6.0);
+    e = fma(e, x, 0.5);
+    e = fma(e, x, 1.0);
+    return fma(e, x, 1.0);
+}
+
+// F[m] = theta F_m(T), m = 0..L (L a compile-time order)
 template <int L>
-__device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double* F)
+__device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double theta, double* F)
 {
     constexpr double kPi = 3.14159265358979323846;
     if (T < BOYS_TMAX) {
         const int k = __double2int_rn(T * BOYS_GRID);
         const double x = k * (1.0 / BOYS_GRID) - T;
-        const double* t = tab + k * BOYS_NM + L;
+        const double* t = tab + ((size_t)k * BOYS_MT + L) * BOYS_NTAYLOR;
         double f = __ldg(t + BOYS_NTAYLOR - 1);
 #pragma unroll
-        for (int j = BOYS_NTAYLOR - 2; j >= 0; j--) f = __ldg(t + j) + f * x * (1.0 / (j + 1));
-        F[L] = f;
+        for (int j = BOYS_NTAYLOR - 2; j >= 0; j--) f = fma(f, x, __ldg(t + j));
+        F[L] = theta * f;
         if (L > 0) {
-            const double e = exp(-T);
+            const double te = theta * __ldg(tab + BOYS_NT * BOYS_MT * BOYS_NTAYLOR + k) * exp_poly(x);
             const double t2 = 2.0 * T;
 #pragma unroll
-            for (int m = L - 1; m >= 0; m--) F[m] = (t2 * F[m + 1] + e) * (1.0 / (2 * m + 1));
+            for (int m = L - 1; m >= 0; m--) F[m] = fma(t2, F[m + 1], te) * (1.0 / (2 * m + 1));
         }
     } else {
         const double it = 1.0 / T;
-        F[0] = 0.5 * sqrt(kPi * it);
+        F[0] = theta * 0.5 * sqrt(kPi * it);
         if (L > 0) {
-            const double e = exp(-T);
+            const double te = theta * exp(-T);
             const double h = 0.5 * it;
 #pragma unroll
-            for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - e) * h;
+            for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - te) * h;
         }
     }
 }
 
-// runtime-order version (1e integrals, tape kernels)
-__device__ __forceinline__ void boys_eval_n(int L, double T, const double* __restrict__ tab, double* F)
+template <int L>
+__device__ __forceinline__ void boys_eval(float T, const float* __restrict__ tab, float theta, float* F)
+{
+    constexpr float kPi = 3.14159265358979f;
+    if (T < (float)BOYS_TMAX) {
+        const int k = __float2int_rn(T * BOYS_GRID);
+        const float x = k * (1.0f / BOYS_GRID) - T;
+        const float* t = tab + ((size_t)k * BOYS_MT + L) * BOYS_NTAYLOR_F;
+        float f = __ldg(t + 3);
+        f = fmaf(f, x, __ldg(t + 2));
+        f = fmaf(f, x, __ldg(t + 1));
+        f = fmaf(f, x, __ldg(t));
+        F[L] = theta * f;
+        if (L > 0) {
+            // e^x to third order, |x| <= 1/32
+            const float ex = fmaf(fmaf(fmaf(1.0f / 6.0f, x, 0.5f), x, 1.0f), x, 1.0f);
+            const float te = theta * __ldg(tab + BOYS_NT * BOYS_MT * BOYS_NTAYLOR_F + k) * ex;
+            const float t2 = 2.0f * T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; m--) F[m] = fmaf(t2, F[m + 1], te) * (1.0f / (2 * m + 1));
+        }
+    } else {
+        const float it = 1.0f / T;
+        F[0] = theta * 0.5f * sqrtf(kPi * it);
+        if (L > 0) {
+            const float te = theta * __expf(-T);
+            const float h = 0.5f * it;
+#pragma unroll
+            for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - te) * h;
+        }
+    }
+}
+
+// runtime-order version (one-electron integrals, tape kernels)
+__device__ __forceinline__ void boys_eval_n(int L, double T, const double* __restrict__ tab, double theta, double* F)
 {
     constexpr double kPi = 3.14159265358979323846;
     if (T < BOYS_TMAX) {
         const int k = __double2int_rn(T * BOYS_GRID);
         const double x = k * (1.0 / BOYS_GRID) - T;
-        const double* t = tab + k * BOYS_NM + L;
+        const double* t = tab + ((size_t)k * BOYS_MT + L) * BOYS_NTAYLOR;
         double f = __ldg(t + BOYS_NTAYLOR - 1);
 #pragma unroll
-        for (int j = BOYS_NTAYLOR - 2; j >= 0; j--) f = __ldg(t + j) + f * x * (1.0 / (j + 1));
-        F[L] = f;
+        for (int j = BOYS_NTAYLOR - 2; j >= 0; j--) f = fma(f, x, __ldg(t + j));
+        F[L] = theta * f;
         if (L > 0) {
-            const double e = exp(-T);
+            const double te = theta * __ldg(tab + BOYS_NT * BOYS_MT * BOYS_NTAYLOR + k) * exp_poly(x);
             const double t2 = 2.0 * T;
-            for (int m = L - 1; m >= 0; m--) F[m] = (t2 * F[m + 1] + e) / (2 * m + 1);
+            for (int m = L - 1; m >= 0; m--) F[m] = fma(t2, F[m + 1], te) / (2 * m + 1);
         }
     } else {
         const double it = 1.0 / T;
-        F[0] = 0.5 * sqrt(kPi * it);
+        F[0] = theta * 0.5 * sqrt(kPi * it);
         if (L > 0) {
-            const double e = exp(-T);
+            const double te = theta * exp(-T);
             const double h = 0.5 * it;
-            for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - e) * h;
+            for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - te) * h;
         }
     }
 }

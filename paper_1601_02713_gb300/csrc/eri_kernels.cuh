@@ -99,48 +99,58 @@ __device__ __forceinline__ void sph_to_cart4_t(T* __restrict__ buf, T* __restric
 }
 
 // Per-primitive-quartet quantities of the Obara-Saika recursion.
-struct PrimQuartet {
-    double PA[3], WP[3], QC[3], WQ[3];
-    double o2p, o2pr, o2q, o2qr, o2pq, T, theta;
+template <typename R>
+struct PrimQ {
+    R PA[3], WP[3], QC[3], WQ[3];
+    R o2p, o2pr, o2q, o2qr, o2pq, T, theta;
 };
+typedef PrimQ<double> PrimQuartet;
 
-__device__ __forceinline__ void prim_quartet(const double* bra, const double* ket, const double A[3],
-                                             const double C[3], PrimQuartet& g)
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+
+// bra/ket: the first PP_NERI primitive-pair fields (p, P, K, P - A, 1/(2p), 1/(2p^2))
+template <typename R>
+__device__ __forceinline__ void prim_quartet(const R* bra, const R* ket, PrimQ<R>& g)
 {
-    // bra/ket: p, 1/p, Px, Py, Pz, K
-    const double p = bra[0], ip = bra[1], q = ket[0], iq = ket[1];
-    const double rs = rsqrt(p + q);
-    const double ipq = rs * rs;
-    const double rho = p * q * ipq;
-    double PQ2 = 0.0;
-#pragma unroll
-    for (int x = 0; x < 3; x++) {
-        const double P = bra[2 + x], Q = ket[2 + x];
-        const double W = (p * P + q * Q) * ipq;
-        g.PA[x] = P - A[x];
-        g.WP[x] = W - P;
-        g.QC[x] = Q - C[x];
-        g.WQ[x] = W - Q;
-        PQ2 += (P - Q) * (P - Q);
-    }
-    g.T = rho * PQ2;
-    g.o2p = 0.5 * ip;
-    g.o2pr = g.o2p * rho * ip;
-    g.o2q = 0.5 * iq;
-    g.o2qr = g.o2q * rho * iq;
-    g.o2pq = 0.5 * ipq;
-    g.theta = bra[5] * ket[5] * rs;
+    const R p = bra[PP_P], q = ket[PP_P];
+    const R rs = rsqrt_r(p + q);
+    const R ipq = rs * rs;
+    const R qi = q * ipq, pi = p * ipq;
+    const R rho = p * qi;
+    const R PQx = bra[PP_PX] - ket[PP_PX], PQy = bra[PP_PY] - ket[PP_PY], PQz = bra[PP_PZ] - ket[PP_PZ];
+    // W - P = -q/(p+q) (P - Q), W - Q = p/(p+q) (P - Q)
+    g.WP[0] = -qi * PQx;
+    g.WP[1] = -qi * PQy;
+    g.WP[2] = -qi * PQz;
+    g.WQ[0] = pi * PQx;
+    g.WQ[1] = pi * PQy;
+    g.WQ[2] = pi * PQz;
+    g.PA[0] = bra[PP_PAX];
+    g.PA[1] = bra[PP_PAY];
+    g.PA[2] = bra[PP_PAZ];
+    g.QC[0] = ket[PP_PAX];
+    g.QC[1] = ket[PP_PAY];
+    g.QC[2] = ket[PP_PAZ];
+    g.T = rho * fma(PQx, PQx, fma(PQy, PQy, PQz * PQz));
+    g.o2p = bra[PP_O2P];
+    g.o2pr = rho * bra[PP_O2PP];
+    g.o2q = ket[PP_O2P];
+    g.o2qr = rho * ket[PP_O2PP];
+    g.o2pq = R(0.5) * ipq;
+    g.theta = bra[PP_K] * ket[PP_K] * rs;
 }
 
 __device__ __forceinline__ double atomic_add_d(double* a, double v) { return atomicAdd(a, v); }
 
-// Contract a spherical block with the density and scatter into G'.
-template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void scatter_jk(const double* __restrict__ I, double f, int fa, int fb, int fc, int fd,
-                                           int N, const double* __restrict__ D, double* __restrict__ G)
+// Contract a spherical block with the density and scatter into G' (the
+// contraction in the block's precision R, the accumulation in FP64).
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, int fa, int fb, int fc, int fd,
+                                           int N, const R* __restrict__ D, double* __restrict__ G)
 {
     constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
-    double Dab[na * nb], Dcd[nc * nd], Dac[na * nc], Dad[na * nd], Dbc[nb * nc], Dbd[nb * nd];
+    R Dab[na * nb], Dcd[nc * nd], Dac[na * nc], Dad[na * nd], Dbc[nb * nc], Dbd[nb * nd];
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
@@ -171,123 +181,133 @@ __device__ __forceinline__ void scatter_jk(const double* __restrict__ I, double 
     for (int a = 0; a < na; a++) {
 #pragma unroll
         for (int b = 0; b < nb; b++) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int c = 0; c < nc; c++)
 #pragma unroll
                 for (int d = 0; d < nd; d++) s += Dcd[c * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * s);
+            atomic_add_d(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s);
         }
     }
 #pragma unroll
     for (int c = 0; c < nc; c++)
 #pragma unroll
         for (int d = 0; d < nd; d++) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int a = 0; a < na; a++)
 #pragma unroll
                 for (int b = 0; b < nb; b++) s += Dab[a * nb + b] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * s);
+            atomic_add_d(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * (double)s);
         }
 #pragma unroll
     for (int a = 0; a < na; a++)
 #pragma unroll
         for (int c = 0; c < nc; c++) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int b = 0; b < nb; b++)
 #pragma unroll
                 for (int d = 0; d < nd; d++) s += Dbd[b * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * s);
+            atomic_add_d(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * (double)s);
         }
 #pragma unroll
     for (int b = 0; b < nb; b++)
 #pragma unroll
         for (int c = 0; c < nc; c++) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int a = 0; a < na; a++)
 #pragma unroll
                 for (int d = 0; d < nd; d++) s += Dad[a * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * s);
+            atomic_add_d(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * (double)s);
         }
 #pragma unroll
     for (int a = 0; a < na; a++)
 #pragma unroll
         for (int d = 0; d < nd; d++) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int b = 0; b < nb; b++)
 #pragma unroll
                 for (int c = 0; c < nc; c++) s += Dbc[b * nc + c] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * s);
+            atomic_add_d(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * (double)s);
         }
 #pragma unroll
     for (int b = 0; b < nb; b++)
 #pragma unroll
         for (int d = 0; d < nd; d++) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int a = 0; a < na; a++)
 #pragma unroll
                 for (int c = 0; c < nc; c++) s += Dac[a * nc + c] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * s);
+            atomic_add_d(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * (double)s);
         }
 }
 
-// Load primitive pair data of pair g (fields P, IP, PX, PY, PZ, K) for prim k
-__device__ __forceinline__ void load_pp(const Pairs& P, int g, int k, double* out)
+// first nf primitive-pair fields of pair g, primitive pair k
+__device__ __forceinline__ void load_ppn(const Pairs& P, int g, int k, double* out, int nf)
 {
     const size_t n = P.n;
 #pragma unroll
-    for (int f = 0; f < 6; f++) out[f] = __ldg(P.pp + ((size_t)f * PIMD_MAXPP + k) * n + g);
+    for (int f = 0; f < nf; f++) out[f] = __ldg(P.pp + ((size_t)f * PIMD_MAXPP + k) * n + g);
 }
+__device__ __forceinline__ void load_ppn(const Pairs& P, int g, int k, float* out, int nf)
+{
+    const size_t n = P.n;
+#pragma unroll
+    for (int f = 0; f < nf; f++) out[f] = __ldg(P.ppf + ((size_t)f * PIMD_MAXPP + k) * n + g);
+}
+__device__ __forceinline__ const double* pp_base(const Pairs& P, double) { return P.pp; }
+__device__ __forceinline__ const float* pp_base(const Pairs& P, float) { return P.ppf; }
 
 // contracted Cartesian block of one quartet via the generated recursion
-template <class C>
-__device__ __forceinline__ void quartet_cart(const double (*sbra)[PIMD_MAXPP], int nbra, const Pairs& P, int cd,
+template <class C, typename R>
+__device__ __forceinline__ void quartet_cart(const R (*sbra)[PIMD_MAXPP], int nbra, const Pairs& P, int cd,
                                              const double A[3], const double B[3], const double Cc[3],
-                                             const double Dd[3], const double* __restrict__ boys, double* cart)
+                                             const double Dd[3], const R* __restrict__ boys, R* cart)
 {
-    double acc[C::NE * C::NF];
+    R acc[C::NE * C::NF];
 #pragma unroll
-    for (int i = 0; i < C::NE * C::NF; i++) acc[i] = 0.0;
+    for (int i = 0; i < C::NE * C::NF; i++) acc[i] = R(0);
     const int nket = P.npp[cd];
     for (int j = 0; j < nket; j++) {
-        double ket[6];
-        load_pp(P, cd, j, ket);
+        R ket[PP_NERI];
+        load_ppn(P, cd, j, ket, PP_NERI);
         for (int i = 0; i < nbra; i++) {
-            double bra[6];
+            R bra[PP_NERI];
 #pragma unroll
-            for (int f = 0; f < 6; f++) bra[f] = sbra[f][i];
-            PrimQuartet g;
-            prim_quartet(bra, ket, A, Cc, g);
-            double F[C::L + 1];
-            boys_eval<C::L>(g.T, boys, F);
-#pragma unroll
-            for (int m = 0; m <= C::L; m++) F[m] *= g.theta;
-            C::template vrr<double>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1], g.QC[2], g.WQ[0],
-                g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, acc);
+            for (int f = 0; f < PP_NERI; f++) bra[f] = sbra[f][i];
+            PrimQ<R> g;
+            prim_quartet<R>(bra, ket, g);
+            R F[C::L + 1];
+            boys_eval<C::L>(g.T, boys, g.theta, F);
+            C::template vrr<R>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1], g.QC[2],
+                               g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, acc);
         }
     }
-    C::template hrr<double>(acc, A[0] - B[0], A[1] - B[1], A[2] - B[2], Cc[0] - Dd[0], Cc[1] - Dd[1], Cc[2] - Dd[2], cart);
+    C::template hrr<R>(acc, R(A[0] - B[0]), R(A[1] - B[1]), R(A[2] - B[2]), R(Cc[0] - Dd[0]), R(Cc[1] - Dd[1]),
+                       R(Cc[2] - Dd[2]), cart);
 }
 
-// Fock (G') build over the quartets of one class pair. blockDim.x == 128.
-template <class C>
-__global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
-                                                 const double* __restrict__ Dall, double* __restrict__ Gall,
-                                                 const double* __restrict__ boys, double tau,
+// Fock (G') build over the quartets of one class pair whose density-weighted
+// Schwarz bound lies in [tau_lo, tau_hi), in precision R (FP64, or FP32 for
+// the small quartets of the mixed mode). blockDim.x == 128.
+// cnt: executed quartets and primitive quartets.
+template <class C, typename R>
+__global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, const Tile* __restrict__ tiles,
+                                                 const R* __restrict__ Dall, double* __restrict__ Gall,
+                                                 const R* __restrict__ boys, double tau_lo, double tau_hi,
                                                  const double* __restrict__ Dsh, unsigned long long* __restrict__ cnt)
 {
-    __shared__ double sbra[6][PIMD_MAXPP];
+    __shared__ R sbra[PP_NERI][PIMD_MAXPP];
     const Tile t = tiles[blockIdx.x];
-    if (!R.active[t.rep]) return;
+    if (!R_.active[t.rep]) return;
     const int ab = t.ab;
-    if (threadIdx.x < 6 * PIMD_MAXPP) {
+    if (threadIdx.x < PP_NERI * PIMD_MAXPP) {
         const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
-        sbra[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
+        sbra[f][k] = pp_base(P, R(0))[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     }
     __syncthreads();
     const int cd = t.c0 + threadIdx.x;
@@ -301,12 +321,12 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R, cons
         sd = P.sb[cd];
         // density-weighted Schwarz bound: every contribution of the quartet to
         // G' is at most 2 |(ab|cd)| times one of these six density blocks
-        const double dq = fmax(fmax(fmax(shell_bound(R, Dsh, r, sa, sb), shell_bound(R, Dsh, r, sc, sd)),
-                                    fmax(shell_bound(R, Dsh, r, sa, sc), shell_bound(R, Dsh, r, sa, sd))),
-                               fmax(shell_bound(R, Dsh, r, sb, sc), shell_bound(R, Dsh, r, sb, sd)));
-        work = P.Q[ab] * P.Q[cd] * dq >= tau;
+        const double dq = fmax(fmax(fmax(shell_bound(R_, Dsh, r, sa, sb), shell_bound(R_, Dsh, r, sc, sd)),
+                                    fmax(shell_bound(R_, Dsh, r, sa, sc), shell_bound(R_, Dsh, r, sa, sd))),
+                               fmax(shell_bound(R_, Dsh, r, sb, sc), shell_bound(R_, Dsh, r, sb, sd)));
+        const double bound = P.Q[ab] * P.Q[cd] * dq;
+        work = bound >= tau_lo && bound < tau_hi;
     }
-    // executed quartets and primitive quartets of this class (work counters)
     const unsigned nq = __reduce_add_sync(0xffffffffu, work ? 1u : 0u);
     const unsigned np = __reduce_add_sync(0xffffffffu, work ? (unsigned)(P.npp[ab] * P.npp[cd]) : 0u);
     if ((threadIdx.x & 31) == 0 && nq) {
@@ -323,17 +343,17 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R, cons
         Dd[x] = S.xyz[3 * sd + x];
     }
     constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
-    double cart[NCART], tmp[NCART];
-    quartet_cart<C>(sbra, P.npp[ab], P, cd, A, B, Cc, Dd, boys, cart);
+    R cart[NCART], tmp[NCART];
+    quartet_cart<C, R>(sbra, P.npp[ab], P, cd, A, B, Cc, Dd, boys, cart);
     cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
     double f = 1.0;
     if (sa == sb) f *= 0.5;
     if (sc == sd) f *= 0.5;
     if (ab == cd) f *= 0.5;
-    const int N = R.nbf[r];
-    const size_t off = R.moff[r];
-    scatter_jk<C::LA, C::LB, C::LC, C::LD>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
-                                           Gall + off);
+    const int N = R_.nbf[r];
+    const size_t off = R_.moff[r];
+    scatter_jk<C::LA, C::LB, C::LC, C::LD, R>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
+                                              Gall + off);
 }
 
 // Schwarz factors: Q_ab = sqrt(max over functions of (mn|mn)), one thread per pair
@@ -345,10 +365,10 @@ __global__ void __launch_bounds__(128) schwarz_kernel(Pairs P, Shells S, const i
     if (idx >= n) return;
     const int ab = list[idx];
     const int sa = P.sa[ab], sb = P.sb[ab];
-    double sbra_l[6][PIMD_MAXPP];
+    double sbra_l[PP_NERI][PIMD_MAXPP];
     const int np = P.npp[ab];
     for (int k = 0; k < np; k++)
-        for (int f = 0; f < 6; f++) sbra_l[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
+        for (int f = 0; f < PP_NERI; f++) sbra_l[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     double A[3], B[3];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
@@ -357,7 +377,7 @@ __global__ void __launch_bounds__(128) schwarz_kernel(Pairs P, Shells S, const i
     }
     constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
     double cart[NCART], tmp[NCART];
-    quartet_cart<C>(sbra_l, np, P, ab, A, B, A, B, boys, cart);
+    quartet_cart<C, double>(sbra_l, np, P, ab, A, B, A, B, boys, cart);
     cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
     constexpr int na = nsph(C::LA), nb = nsph(C::LB);
     double m = 0.0;

@@ -63,12 +63,19 @@ def pick_dir(v):
 
 
 class VRRGen:
-    """Demand-driven [e0|f0]^(m) generator."""
+    """Demand-driven [e0|f0]^(m) generator. Nodes are kept structured so that
+    each recursion step can be emitted as one chain of fused multiply-adds
+    with the integer factors folded into pre-scaled constants."""
 
     def __init__(self):
         self.memo = {}
-        self.lines = []
+        self.nodes = []      # (name, kind, i, t1, t2, k1, t3, t4, k2, t5)
+        self.uses = {}
         self.n = 0
+
+    def _use(self, t):
+        if t is not None:
+            self.uses[t] = self.uses.get(t, 0) + 1
 
     def get(self, e, f, m):
         if min(e) < 0 or min(f) < 0:
@@ -80,41 +87,63 @@ class VRRGen:
             name = f"F{m}"
             self.memo[key] = name
             return name
+        t3 = t4 = t5 = None
+        k1 = k2 = 0
         if sum(f) > 0:
+            kind = "ket"
             i = pick_dir(f)
             f1 = sub(f, i)
-            terms = []
-            t1 = self.get(e, f1, m)
-            t2 = self.get(e, f1, m + 1)
-            terms.append(f"QC{i}*{t1}")
-            terms.append(f"WQ{i}*{t2}")
+            t1, t2 = self.get(e, f1, m), self.get(e, f1, m + 1)
             if f1[i] > 0:
                 f2 = sub(f1, i)
-                t3 = self.get(e, f2, m)
-                t4 = self.get(e, f2, m + 1)
-                k = f1[i]
-                terms.append(f"R({k})*(o2q*{t3} - o2qr*{t4})" if k > 1 else f"(o2q*{t3} - o2qr*{t4})")
+                t3, t4, k1 = self.get(e, f2, m), self.get(e, f2, m + 1), f1[i]
             if e[i] > 0:
-                t5 = self.get(sub(e, i), f1, m + 1)
-                k = e[i]
-                terms.append(f"R({k})*o2pq*{t5}" if k > 1 else f"o2pq*{t5}")
+                t5, k2 = self.get(sub(e, i), f1, m + 1), e[i]
         else:
+            kind = "bra"
             i = pick_dir(e)
             e1 = sub(e, i)
-            t1 = self.get(e1, f, m)
-            t2 = self.get(e1, f, m + 1)
-            terms = [f"PA{i}*{t1}", f"WP{i}*{t2}"]
+            t1, t2 = self.get(e1, f, m), self.get(e1, f, m + 1)
             if e1[i] > 0:
                 e2 = sub(e1, i)
-                t3 = self.get(e2, f, m)
-                t4 = self.get(e2, f, m + 1)
-                k = e1[i]
-                terms.append(f"R({k})*(o2p*{t3} - o2pr*{t4})" if k > 1 else f"(o2p*{t3} - o2pr*{t4})")
+                t3, t4, k1 = self.get(e2, f, m), self.get(e2, f, m + 1), e1[i]
+        for t in (t1, t2, t3, t4, t5):
+            self._use(t)
         name = f"v{self.n}"
         self.n += 1
-        self.lines.append(f"const R {name} = " + " + ".join(terms) + ";")
+        self.nodes.append((name, kind, i, t1, t2, k1, t3, t4, k2, t5))
         self.memo[key] = name
         return name
+
+    @staticmethod
+    def const(base, k, used):
+        if k == 1:
+            return base
+        used.add((base, k))
+        return f"{base}_{k}"
+
+    def expr(self, node, addend, used):
+        """FMA chain of one recursion step; `addend` (or None) is added last.
+        Returns (expression, flop count)."""
+        name, kind, i, t1, t2, k1, t3, t4, k2, t5 = node
+        if kind == "bra":
+            a1, a2, c1, c2 = f"PA{i}", f"WP{i}", "o2p", "o2pr"
+        else:
+            a1, a2, c1, c2 = f"QC{i}", f"WQ{i}", "o2q", "o2qr"
+        inner = addend
+        fl = 0
+        if t5 is not None:
+            c = self.const("o2pq", k2, used)
+            inner = f"fma({c}, {t5}, {inner})" if inner else f"{c}*{t5}"
+            fl += 2 if addend or inner.startswith("fma") else 1
+        if t3 is not None:
+            ca, cb = self.const(c1, k1, used), self.const(c2, k1, used)
+            inner = f"fma(-{cb}, {t4}, {inner})" if inner else f"-({cb}*{t4})"
+            inner = f"fma({ca}, {t3}, {inner})"
+            fl += 4
+        inner = f"fma({a2}, {t2}, {inner})" if inner else f"{a2}*{t2}"
+        fl += 2
+        return f"fma({a1}, {t1}, {inner})", fl + 2
 
 
 def level_range(lo, hi):
@@ -127,17 +156,41 @@ def level_range(lo, hi):
 def gen_vrr(name, Ltot, acc_sets, grad_sig=False):
     """acc_sets: list of (acc_name, e_lo, e_hi, f_lo, f_hi, weight_expr or None).
     Emits a device function adding [e0|f0]^(0) for every listed (e, f) into
-    acc_name[idx] (times weight)."""
+    acc_name[idx] (times weight). A target that no other step reads and that
+    is accumulated once without weight is accumulated inside its own FMA chain."""
     g = VRRGen()
-    body_acc = []
+    targets = []
     for acc, elo, ehi, flo, fhi, w in acc_sets:
         es = level_range(elo, ehi)
         fs = level_range(flo, fhi)
         for ie, e in enumerate(es):
             for jf, f in enumerate(fs):
-                v = g.get(e, f, 0)
-                idx = ie * len(fs) + jf
-                body_acc.append(f"{acc}[{idx}] += {w}*{v};" if w else f"{acc}[{idx}] += {v};")
+                targets.append((acc, ie * len(fs) + jf, w, g.get(e, f, 0)))
+    tcount = {}
+    for _, _, _, v in targets:
+        tcount[v] = tcount.get(v, 0) + 1
+    fold = {}
+    for acc, idx, w, v in targets:
+        if w is None and tcount[v] == 1 and g.uses.get(v, 0) == 0 and v.startswith("v"):
+            fold[v] = f"{acc}[{idx}]"
+    used = set()
+    lines = []
+    nflop = 0
+    for node in g.nodes:
+        nm = node[0]
+        if nm in fold:
+            ex, fl = g.expr(node, fold[nm], used)
+            lines.append(f"{fold[nm]} = {ex};")
+        else:
+            ex, fl = g.expr(node, None, used)
+            lines.append(f"const R {nm} = {ex};")
+        nflop += fl
+    body_acc = []
+    for acc, idx, w, v in targets:
+        if v in fold:
+            continue
+        body_acc.append(f"{acc}[{idx}] = fma({w}, {v}, {acc}[{idx}]);" if w else f"{acc}[{idx}] += {v};")
+        nflop += 2 if w else 1
     if grad_sig:
         args = "R* __restrict__ accU, R* __restrict__ accA, R* __restrict__ accB, R* __restrict__ accC, R wa, R wb, R wc"
     else:
@@ -147,9 +200,10 @@ def gen_vrr(name, Ltot, acc_sets, grad_sig=False):
            f"R o2p, R o2pr, R o2q, R o2qr, R o2pq, {args})\n{{\n")
     used_m = sorted({int(k[2]) for k in g.memo if sum(k[0]) == 0 and sum(k[1]) == 0})
     pre = "".join(f"    const R F{m} = Fm[{m}];\n" for m in used_m)
-    body = "\n".join("    " + l for l in g.lines + body_acc)
-    nflop = sum(l.count("*") + l.count("+") + l.count(" - ") for l in g.lines) + len(body_acc) * 2
-    return hdr + pre + body + "\n}\n", len(g.lines), nflop
+    pre += "".join(f"    const R {b}_{k} = R({k}) * {b};\n" for b, k in sorted(used))
+    nflop += len(used)
+    body = "\n".join("    " + l for l in lines + body_acc)
+    return hdr + pre + body + "\n}\n", len(g.nodes), nflop
 
 
 class HRRGen:
@@ -390,6 +444,174 @@ def gen_tape(c):
 HRR_NAMES = ["Ap", "Bp", "Cp", "Am", "Bm", "Cm"]
 
 
+# ---------------------------------------------------------------------------
+# Level-scheduled tapes for the warp-cooperative kernels of the largest
+# classes: every intermediate lives in shared memory and the ops of one
+# dependency level are independent, so the 32 lanes of a warp execute a level
+# in parallel. Slot layout: [0, NACC) accumulators, then F_m at F0 .. F0+L,
+# then VRR intermediates; the HRR intermediates reuse the space from F0 on.
+# Op = 8 ints {kind, dst, s1, s2, s3, s4, s5, aux}:
+#   kind 0/1: bra/ket VRR (aux = dir | k1 << 4 | k2 << 8), kind 3/4: bra/ket HRR
+#   (aux = dir); accumulation op = 4 ints {dst, src, weight, 0}.
+# ---------------------------------------------------------------------------
+COOP_ENERGY_MIN_VRR = 2000
+COOP_GRAD_MIN_VRR = HEAVY_GRAD_VRR_LINES
+
+
+def _sort_levels(ops, base_level):
+    """Stable sort of ops by dependency level; returns (ops, level offsets)."""
+    lvl = dict(base_level)
+    out = []
+    for op in ops:
+        srcs = [x for x in op[2:7] if x >= 0]
+        lv = 1 + max((lvl.get(x, 0) for x in srcs), default=0)
+        lvl[op[1]] = lv
+        out.append((lv, op))
+    out.sort(key=lambda t: t[0])
+    offs = [0]
+    cur = 1
+    for i, (lv, _) in enumerate(out):
+        while lv > cur:
+            offs.append(i)
+            cur += 1
+    offs.append(len(out))
+    return [o for _, o in out], offs
+
+
+def gen_coop(c, grad):
+    la, lb, lc, ld = c
+    L = la + lb + lc + ld + (1 if grad else 0)
+    sets = grad_sets(c) if grad else [("acc", la, la + lb, lc, lc + ld, None)]
+    acc_base, nacc = {}, 0
+    for name, elo, ehi, flo, fhi, w in sets:
+        acc_base[name] = nacc
+        nacc += n_range(elo, ehi) * n_range(flo, fhi)
+    F0 = nacc
+    nxt = [F0 + L + 1]
+    ops, memo = [], {}
+
+    def new():
+        v = nxt[0]
+        nxt[0] += 1
+        return v
+
+    def get(e, f, m):
+        if min(e) < 0 or min(f) < 0:
+            return -1
+        key = (e, f, m)
+        if key in memo:
+            return memo[key]
+        if sum(e) == 0 and sum(f) == 0:
+            memo[key] = F0 + m
+            return F0 + m
+        if sum(f) > 0:
+            i = pick_dir(f)
+            f1 = sub(f, i)
+            s1, s2 = get(e, f1, m), get(e, f1, m + 1)
+            s3 = s4 = -1
+            k1 = 0
+            if f1[i] > 0:
+                f2 = sub(f1, i)
+                s3, s4 = get(e, f2, m), get(e, f2, m + 1)
+                k1 = f1[i]
+            s5, k2 = -1, 0
+            if e[i] > 0:
+                s5, k2 = get(sub(e, i), f1, m + 1), e[i]
+            d = new()
+            ops.append((1, d, s1, s2, s3, s4, s5, i | (k1 << 4) | (k2 << 8)))
+        else:
+            i = pick_dir(e)
+            e1 = sub(e, i)
+            s1, s2 = get(e1, f, m), get(e1, f, m + 1)
+            s3 = s4 = -1
+            k1 = 0
+            if e1[i] > 0:
+                e2 = sub(e1, i)
+                s3, s4 = get(e2, f, m), get(e2, f, m + 1)
+                k1 = e1[i]
+            d = new()
+            ops.append((0, d, s1, s2, s3, s4, -1, i | (k1 << 4)))
+        memo[key] = d
+        return d
+
+    wsel = {None: 0, "wa": 1, "wb": 2, "wc": 3}
+    accops = []
+    for name, elo, ehi, flo, fhi, w in sets:
+        es, fs = level_range(elo, ehi), level_range(flo, fhi)
+        for ie, e in enumerate(es):
+            for jf, f in enumerate(fs):
+                accops.append((acc_base[name] + ie * len(fs) + jf, get(e, f, 0), wsel[w], 0))
+    vrr_ops, vrr_lv = _sort_levels(ops, {F0 + m: 0 for m in range(L + 1)})
+    nwork = nxt[0] - F0
+    # HRR tapes: the class itself (energy) or the six shifted classes (gradient)
+    targets = grad_hrrs(c) if grad else [("E", c, "acc")]
+    hrrs = []
+    for hname, (a_, b_, c_, d_), src in targets:
+        elo, ehi, flo, fhi = set_range(sets, src)
+        es, fs = level_range(elo, ehi), level_range(flo, fhi)
+        eidx = {e: i for i, e in enumerate(es)}
+        fidx = {f: i for i, f in enumerate(fs)}
+        hm, hops = {}, []
+        hn = [F0]
+
+        def hget(a, b, cc, dd):
+            key = (a, b, cc, dd)
+            if key in hm:
+                return hm[key]
+            if sum(b) == 0 and sum(dd) == 0:
+                v = acc_base[src] + eidx[a] * len(fs) + fidx[cc]
+                hm[key] = v
+                return v
+            if sum(dd) > 0:
+                i = pick_dir(dd)
+                d1 = sub(dd, i)
+                s1, s2 = hget(a, b, add(cc, i), d1), hget(a, b, cc, d1)
+                kind = 4
+            else:
+                i = pick_dir(b)
+                b1 = sub(b, i)
+                s1, s2 = hget(add(a, i), b1, cc, dd), hget(a, b1, cc, dd)
+                kind = 3
+            dst = hn[0]
+            hn[0] += 1
+            hops.append((kind, dst, s1, s2, -1, -1, -1, i))
+            hm[key] = dst
+            return dst
+
+        outs = [hget(a, b, cc, dd) for a in carts(a_) for b in carts(b_) for cc in carts(c_) for dd in carts(d_)]
+        sops, slv = _sort_levels(hops, {})
+        hrrs.append((hname, sops, slv, outs))
+        nwork = max(nwork, hn[0] - F0)
+    return dict(L=L, nacc=nacc, F0=F0, nwork=nwork, vrr=vrr_ops, vrr_lv=vrr_lv, acc=accops, hrrs=hrrs)
+
+
+def coop_header(nm, grad, t):
+    """C++ header with the tape arrays of one class (host data, uploaded by
+    the class's translation unit)."""
+    pre = f"coop{'g' if grad else 'e'}_{nm}"
+
+    def arr(name, flat):
+        flat = [str(x) for x in flat]
+        lines = [", ".join(flat[i:i + 24]) for i in range(0, len(flat), 24)] or ["0"]
+        return f"static const int {name}[] = {{\n" + ",\n".join(lines) + "\n};\n"
+
+    out = [f"// Generated by gen_eri.py: level-scheduled {'gradient' if grad else 'Fock'} tape of class {nm}.\n",
+           "#pragma once\n\n"]
+    out.append(arr(f"{pre}_vrr", [x for op in t["vrr"] for x in op]))
+    out.append(arr(f"{pre}_vrr_lv", t["vrr_lv"]))
+    out.append(arr(f"{pre}_acc", [x for op in t["acc"] for x in op]))
+    names = []
+    for hname, sops, slv, outs in t["hrrs"]:
+        out.append(arr(f"{pre}_hrr{hname}", [x for op in sops for x in op]))
+        out.append(arr(f"{pre}_hrr{hname}_lv", slv))
+        out.append(arr(f"{pre}_out{hname}", outs))
+        names.append((hname, len(sops), len(slv) - 1, len(outs)))
+    out.append(f"struct Coop{'G' if grad else 'E'}_{nm} {{ static constexpr int L={t['L']}, NACC={t['nacc']}, "
+               f"F0={t['F0']}, NWORK={t['nwork']}, NVRR={len(t['vrr'])}, NVLEV={len(t['vrr_lv']) - 1}, "
+               f"NACCOP={len(t['acc'])}; }};\n")
+    return "".join(out), names
+
+
 def write_if_changed(path, text):
     """Write text to path unless the file already holds exactly that text
     (keeps timestamps and build caches stable)."""
@@ -409,7 +631,6 @@ def generate(outdir):
     import os
     os.makedirs(outdir, exist_ok=True)
     stats = []
-    tape_all = []
     for c in classes():
         la, lb, lc, ld = c
         nm = cls_name(c)
@@ -423,6 +644,10 @@ def generate(outdir):
         parts.append(hcode)
         parts.append("};\n")
         write_if_changed(os.path.join(outdir, f"eri_{nm}.cuh"), "".join(parts))
+        coop_e = nl > COOP_ENERGY_MIN_VRR
+        if coop_e:
+            hdr, _ = coop_header(nm, False, gen_coop(c, False))
+            write_if_changed(os.path.join(outdir, f"coope_{nm}.cuh"), hdr)
         sets = grad_sets(c)
         gcode, gnl, gnfl = gen_vrr("vrr", L + 1, sets, grad_sig=True)
         heavy = gnl > HEAVY_GRAD_VRR_LINES
@@ -442,29 +667,9 @@ def generate(outdir):
         gparts.append("};\n")
         write_if_changed(os.path.join(outdir, f"grad_{nm}.cuh"), "".join(gparts))
         if heavy:
-            tape_all.append((nm, gen_tape(c)))
-        stats.append((nm, nl, nfl, nh, gnl, gnfl, heavy))
-    # tapes: one header per heavy class with the op arrays (host side; the
-    # class's translation unit uploads them)
-    for nm, (ops, accops, hops, nslot, accb, outs, nvrr) in tape_all:
-        def arr(name, rows):
-            flat = [str(x) for r in rows for x in r]
-            lines = []
-            for i in range(0, len(flat), 24):
-                lines.append(", ".join(flat[i:i + 24]))
-            return f"static const int {name}[] = {{\n" + ",\n".join(lines) + "\n};\n"
-        tp = [f"// Generated by gen_eri.py: op tape of the gradient of class {nm}.\n"
-              "// Op = 8 ints {kind, dst, s1, s2, s3, s4, s5, aux}; kind 0/1 bra/ket VRR,\n"
-              "// 2 accumulate (aux = weight), 3/4 bra/ket HRR (aux = direction).\n#pragma once\n\n"]
-        tp.append(arr("tape_vrr", ops))
-        tp.append(arr("tape_acc", accops))
-        tp.append(arr("tape_hrr", hops))
-        for hname in HRR_NAMES:
-            vals = outs.get(hname, [0])
-            tp.append(f"static const int tape_out{hname}[] = {{" + ", ".join(map(str, vals)) + "};\n")
-        tp.append(f"struct Tape_{nm} {{ static constexpr int NVRR={len(ops)}, NACC={len(accops)}, "
-                  f"NHRR={len(hops)}, NSLOT={nslot}; }};\n")
-        write_if_changed(os.path.join(outdir, f"grad_tape_{nm}.cuh"), "".join(tp))
+            hdr, _ = coop_header(nm, True, gen_coop(c, True))
+            write_if_changed(os.path.join(outdir, f"coopg_{nm}.cuh"), hdr)
+        stats.append((nm, nl, nfl, nh, gnl, gnfl, heavy, coop_e))
     return stats
 
 

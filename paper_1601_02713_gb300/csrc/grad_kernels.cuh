@@ -106,13 +106,6 @@ struct ArrAcc {
     __device__ __forceinline__ double operator()(int i) const { return p[i]; }
 };
 
-// load the 8 primitive-pair fields (P, IP, PX, PY, PZ, K, EA, EB)
-__device__ __forceinline__ void load_pp8(const Pairs& P, int g, int k, double* out)
-{
-    const size_t n = P.n;
-#pragma unroll
-    for (int f = 0; f < 8; f++) out[f] = __ldg(P.pp + ((size_t)f * PIMD_MAXPP + k) * n + g);
-}
 
 __device__ __forceinline__ void scatter_grad(double* grad, const Shells& S, int sa, int sb, int sc, int sd,
                                              const double gA[3], const double gB[3], const double gC[3])
@@ -144,10 +137,10 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, 
                                                      const double* __restrict__ Dsh)
 {
     constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
-    __shared__ double sbra[8][PIMD_MAXPP];
+    __shared__ double sbra[PP_NF][PIMD_MAXPP];
     const Tile t = tiles[blockIdx.x];
     const int ab = t.ab;
-    if (threadIdx.x < 8 * PIMD_MAXPP) {
+    if (threadIdx.x < PP_NF * PIMD_MAXPP) {
         const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
         sbra[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     }
@@ -171,21 +164,19 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, 
     for (int i = 0; i < G::N_accC; i++) accC[i] = 0.0;
     const int nbra = P.npp[ab], nket = P.npp[cd];
     for (int j = 0; j < nket; j++) {
-        double ket[8];
-        load_pp8(P, cd, j, ket);
+        double ket[PP_NF];
+        load_ppn(P, cd, j, ket, PP_NF);
         for (int i = 0; i < nbra; i++) {
-            double bra[6];
+            double bra[PP_NERI];
 #pragma unroll
-            for (int f = 0; f < 6; f++) bra[f] = sbra[f][i];
+            for (int f = 0; f < PP_NERI; f++) bra[f] = sbra[f][i];
             PrimQuartet g;
-            prim_quartet(bra, ket, A, Cc, g);
+            prim_quartet(bra, ket, g);
             double F[G::L + 1];
-            boys_eval<G::L>(g.T, boys, F);
-#pragma unroll
-            for (int m = 0; m <= G::L; m++) F[m] *= g.theta;
+            boys_eval<G::L>(g.T, boys, g.theta, F);
             G::template vrr<double>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1],
                                     g.QC[2], g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, accU,
-                                    accA, accB, accC, 2.0 * sbra[6][i], 2.0 * sbra[7][i], 2.0 * ket[6]);
+                                    accA, accB, accC, 2.0 * sbra[PP_EA][i], 2.0 * sbra[PP_EB][i], 2.0 * ket[PP_EA]);
         }
     }
     const double AB0 = A[0] - B[0], AB1 = A[1] - B[1], AB2 = A[2] - B[2];
@@ -233,129 +224,6 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, 
         }
     }
     scatter_grad(grad, S, sa, sb, sc, sd, gA, gB, gC);
-}
-
-// ---------------------------------------------------------------------------
-// Tape interpreter for the gradient classes whose straight-line code would be
-// too large: the same recursions, read as op lists, with every intermediate in
-// a per-thread slice of a global scratch buffer laid out [slot][thread] so that
-// a warp's accesses coalesce. Persistent grid; blockDim.x == 128.
-// ---------------------------------------------------------------------------
-struct TapeDev {
-    const int* vrr;   // 8 ints per op
-    const int* acc;
-    const int* hrr;
-    const int* out[6];  // Ap, Bp, Cp, Am, Bm, Cm output slots
-    int nvrr, nacc, nhrr, nslot;
-};
-
-struct ScrAcc {
-    const double* s;
-    const int* slot;
-    size_t stride;
-    __device__ __forceinline__ double operator()(int i) const { return s[(size_t)__ldg(slot + i) * stride]; }
-};
-
-template <class G>
-__global__ void __launch_bounds__(128) grad2e_tape_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
-                                                          int ntiles, const double* __restrict__ Dall,
-                                                          double* __restrict__ grad, const double* __restrict__ boys,
-                                                          double tau, TapeDev tp, double* __restrict__ scratch,
-                                                          const double* __restrict__ Dsh)
-{
-    constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
-    __shared__ double sbra[8][PIMD_MAXPP];
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    double* Sx = scratch + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const Tile t = tiles[tile];
-        const int ab = t.ab;
-        __syncthreads();
-        if (threadIdx.x < 8 * PIMD_MAXPP) {
-            const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
-            sbra[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
-        }
-        __syncthreads();
-        const int cd = t.c0 + threadIdx.x;
-        if (cd >= t.c1) continue;
-        const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
-        if (P.Q[ab] * P.Q[cd] * gamma_bound(R, Dsh, t.rep, sa, sb, sc, sd) < tau) continue;
-        double A[3], B[3], Cc[3], Dd[3];
-#pragma unroll
-        for (int x = 0; x < 3; x++) {
-            A[x] = S.xyz[3 * sa + x];
-            B[x] = S.xyz[3 * sb + x];
-            Cc[x] = S.xyz[3 * sc + x];
-            Dd[x] = S.xyz[3 * sd + x];
-        }
-        for (int o = 0; o < tp.nacc; o++) Sx[(size_t)__ldg(tp.acc + 8 * o + 1) * stride] = 0.0;
-        const int nbra = P.npp[ab], nket = P.npp[cd];
-        for (int j = 0; j < nket; j++) {
-            double ket[8];
-            load_pp8(P, cd, j, ket);
-            for (int i = 0; i < nbra; i++) {
-                double bra[6];
-#pragma unroll
-                for (int f = 0; f < 6; f++) bra[f] = sbra[f][i];
-                PrimQuartet g;
-                prim_quartet(bra, ket, A, Cc, g);
-                double F[G::L + 1];
-                boys_eval<G::L>(g.T, boys, F);
-#pragma unroll
-                for (int m = 0; m <= G::L; m++) Sx[(size_t)m * stride] = F[m] * g.theta;
-                for (int o = 0; o < tp.nvrr; o++) {
-                    const int* op = tp.vrr + 8 * o;
-                    const int kind = __ldg(op), dst = __ldg(op + 1), s1 = __ldg(op + 2), s2 = __ldg(op + 3);
-                    const int s3 = __ldg(op + 4), s4 = __ldg(op + 5), s5 = __ldg(op + 6), aux = __ldg(op + 7);
-                    const int dir = aux & 15, k1 = (aux >> 4) & 15, k2 = aux >> 8;
-                    double v;
-                    if (kind == 0) {
-                        const double pa = dir == 0 ? g.PA[0] : (dir == 1 ? g.PA[1] : g.PA[2]);
-                        const double wp = dir == 0 ? g.WP[0] : (dir == 1 ? g.WP[1] : g.WP[2]);
-                        v = pa * Sx[(size_t)s1 * stride] + wp * Sx[(size_t)s2 * stride];
-                        if (s3 >= 0) v += k1 * (g.o2p * Sx[(size_t)s3 * stride] - g.o2pr * Sx[(size_t)s4 * stride]);
-                    } else {
-                        const double qc = dir == 0 ? g.QC[0] : (dir == 1 ? g.QC[1] : g.QC[2]);
-                        const double wq = dir == 0 ? g.WQ[0] : (dir == 1 ? g.WQ[1] : g.WQ[2]);
-                        v = qc * Sx[(size_t)s1 * stride] + wq * Sx[(size_t)s2 * stride];
-                        if (s3 >= 0) v += k1 * (g.o2q * Sx[(size_t)s3 * stride] - g.o2qr * Sx[(size_t)s4 * stride]);
-                        if (s5 >= 0) v += k2 * g.o2pq * Sx[(size_t)s5 * stride];
-                    }
-                    Sx[(size_t)dst * stride] = v;
-                }
-                const double w[4] = {1.0, 2.0 * sbra[6][i], 2.0 * sbra[7][i], 2.0 * ket[6]};
-                for (int o = 0; o < tp.nacc; o++) {
-                    const int* op = tp.acc + 8 * o;
-                    const int dst = __ldg(op + 1), src = __ldg(op + 2), ws = __ldg(op + 7);
-                    const double wv = ws == 0 ? w[0] : (ws == 1 ? w[1] : (ws == 2 ? w[2] : w[3]));
-                    Sx[(size_t)dst * stride] += wv * Sx[(size_t)src * stride];
-                }
-            }
-        }
-        const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-        const double CD[3] = {Cc[0] - Dd[0], Cc[1] - Dd[1], Cc[2] - Dd[2]};
-        for (int o = 0; o < tp.nhrr; o++) {
-            const int* op = tp.hrr + 8 * o;
-            const int kind = __ldg(op), dst = __ldg(op + 1), s1 = __ldg(op + 2), s2 = __ldg(op + 3);
-            const int dir = __ldg(op + 7);
-            const double c = kind == 3 ? (dir == 0 ? AB[0] : (dir == 1 ? AB[1] : AB[2]))
-                                       : (dir == 0 ? CD[0] : (dir == 1 ? CD[1] : CD[2]));
-            Sx[(size_t)dst * stride] = Sx[(size_t)s1 * stride] + c * Sx[(size_t)s2 * stride];
-        }
-        constexpr int NC = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
-        double Gc[NC], tmp[NC];
-        double f = 1.0;
-        if (sa == sb) f *= 0.5;
-        if (sc == sd) f *= 0.5;
-        if (ab == cd) f *= 0.5;
-        const int r = t.rep;
-        gamma_cart<LA, LB, LC, LD>(f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], R.nbf[r], Dall + R.moff[r], Gc, tmp);
-        double gA[3], gB[3], gC[3];
-        contract_deriv<LA, LB, LC, LD, 0>(Gc, ScrAcc{Sx, tp.out[0], stride}, ScrAcc{Sx, tp.out[3], stride}, gA);
-        contract_deriv<LA, LB, LC, LD, 1>(Gc, ScrAcc{Sx, tp.out[1], stride}, ScrAcc{Sx, tp.out[4], stride}, gB);
-        contract_deriv<LA, LB, LC, LD, 2>(Gc, ScrAcc{Sx, tp.out[2], stride}, ScrAcc{Sx, tp.out[5], stride}, gC);
-        scatter_grad(grad, S, sa, sb, sc, sd, gA, gB, gC);
-    }
 }
 
 }  // namespace pimd

@@ -45,9 +45,12 @@ void class_pair_ls(int cp, int* la, int* lb, int* lc, int* ld);
 // floating-point operations per primitive quartet of class pair cp: the
 // generated recursion plus per-primitive set-up, Boys and prefactor
 long long class_vrr_flops(int cp);
+// Fock build of one class pair: quartets with bound >= max(tau, fp32_tau) in
+// FP64 (D, boys), those in [tau, fp32_tau) in FP32 (Df, boysf); counters
+// cnt[0..1] FP64 quartets / primitive quartets, cnt[2..3] the same in FP32
 void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
-               const double* D, double* G, const double* boys, double tau, const double* Dsh,
-               unsigned long long* cnt, cudaStream_t st);
+               const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau,
+               double fp32_tau, const double* Dsh, unsigned long long* cnt, cudaStream_t st);
 void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n, const double* boys,
                     double* Q, cudaStream_t st);
 // gradient: returns scratch bytes the tape path needs for class pair cp (0 if straight-line)
@@ -56,7 +59,9 @@ void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const
                    const double* D, double* grad, const double* boys, double tau, double* scratch,
                    int grid_blocks, const double* Dsh, cudaStream_t st);
 void grad2e_tapes_upload();   // once per device
-void boys_table_upload(double** dev_tab);
+void boys_table_upload(double** dev_tab, float** dev_tabf);
+// FP32 copies for the mixed-precision quartets
+void launch_to_float(const double* src, float* dst, long long n, cudaStream_t st);
 
 // ------------------------------------------------------------------ linalg
 struct GemmDesc {

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* __restrict__ 
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
 // g_p <- c g_p - s g_q, g_q <- s g_p + c g_q.
 // ---------------------------------------------------------------------------
-constexpr int JAC_THREADS = 1024;
+constexpr int JAC_THREADS = 512;
+constexpr int JAC_PER = 24;   // column elements per lane: n <= 768
 constexpr int JAC_MAXSWEEP = 60;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -149,12 +150,20 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
                 if (p >= n || q >= n) continue;
                 double* gp = G + (size_t)p * n;
                 double* gq = G + (size_t)q * n;
+                // both columns in registers (all loads in flight at once)
+                double x[JAC_PER], y[JAC_PER];
+#pragma unroll
+                for (int k = 0; k < JAC_PER; k++) {
+                    const int i = lane + 32 * k;
+                    x[k] = i < n ? gp[i] : 0.0;
+                    y[k] = i < n ? gq[i] : 0.0;
+                }
                 double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < n; i += 32) {
-                    const double x = gp[i], y = gq[i];
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
+#pragma unroll
+                for (int k = 0; k < JAC_PER; k++) {
+                    al = fma(x[k], x[k], al);
+                    be = fma(y[k], y[k], be);
+                    ga = fma(x[k], y[k], ga);
                 }
                 al = warp_sum(al);
                 be = warp_sum(be);
@@ -164,10 +173,13 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
                     const double zeta = (be - al) / (2.0 * ga);
                     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    for (int i = lane; i < n; i += 32) {
-                        const double x = gp[i], y = gq[i];
-                        gp[i] = c * x - s * y;
-                        gq[i] = s * x + c * y;
+#pragma unroll
+                    for (int k = 0; k < JAC_PER; k++) {
+                        const int i = lane + 32 * k;
+                        if (i < n) {
+                            gp[i] = c * x[k] - s * y[k];
+                            gq[i] = s * x[k] + c * y[k];
+                        }
                     }
                 }
             }
@@ -553,6 +565,8 @@ void launch_gemm(const GemmDesc* d_desc, int ndesc, int maxM, int maxN, const in
 void launch_jacobi(const RepMat* d_rm, int nrep, const double* A, double* V, double* evals, int ldE, double* work,
                    const int* active, int shift_to_spd, cudaStream_t st)
 {
+    // ldE is the largest n of the batch; the kernel holds 32 * JAC_PER column elements per warp
+    if (ldE > 32 * JAC_PER) return;
     if (nrep == 0) return;
     jacobi_kernel<<<nrep, JAC_THREADS, sizeof(double) * ldE, st>>>(d_rm, A, V, evals, ldE, work, active,
                                                                   shift_to_spd);
@@ -630,7 +644,9 @@ void launch_diis_combine(const RepMat* rm, int nrep, const double* Fh, const dou
 int eigh_noalloc(int nmat, int n, const double* A, double* V, double* evals, cudaStream_t st)
 {
     if (nmat <= 0 || n <= 0 || !A || !V || !evals) return -1;
-    if (nmat > PIMD_EIGH_NOALLOC_MAX_MATS || (long long)nmat * n * n > PIMD_EIGH_NOALLOC_MAX_DOUBLES) return -1;
+    if (nmat > PIMD_EIGH_NOALLOC_MAX_MATS || (long long)nmat * n * n > PIMD_EIGH_NOALLOC_MAX_DOUBLES ||
+        n > 32 * JAC_PER)
+        return -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -3;
     if (!g_eigh_work_ptr[dev]) {

@@ -259,14 +259,10 @@ __global__ void pair_data_kernel(Pairs P, int* npp, double* pp, Shells S, BasisP
             const double p = ea + eb, ip = 1.0 / p;
             const double kij = B.coefs[pa + i] * B.coefs[pb + j] * exp(-ea * eb * ip * AB2) * ip;
             if (fabs(kij) < 1e-17 * kmax) continue;
-            const double vals[PP_NF] = {p,
-                                        ip,
-                                        (ea * A[0] + eb * Bc[0]) * ip,
-                                        (ea * A[1] + eb * Bc[1]) * ip,
-                                        (ea * A[2] + eb * Bc[2]) * ip,
-                                        c0 * kij,
-                                        ea,
-                                        eb};
+            const double Px = (ea * A[0] + eb * Bc[0]) * ip, Py = (ea * A[1] + eb * Bc[1]) * ip,
+                         Pz = (ea * A[2] + eb * Bc[2]) * ip;
+            const double vals[PP_NF] = {p,  Px, Py, Pz, c0 * kij, Px - A[0], Py - A[1], Pz - A[2],
+                                        0.5 * ip, 0.5 * ip * ip, ea, eb};
             for (int f = 0; f < PP_NF; f++) pp[((size_t)f * PIMD_MAXPP + k) * P.n + g] = vals[f];
             k++;
         }
@@ -332,7 +328,7 @@ __device__ void one_e_blocks(int sa, int sb, int la, int lb, const Shells& S, co
                     PC2 += PC[x] * PC[x];
                 }
                 double F[NM1];
-                boys_eval_n(la + lb, p * PC2, boys, F);
+                boys_eval_n(la + lb, p * PC2, boys, 1.0, F);
                 os_nuclear(la, lb, p, PA, PB, PC, F, -At.Z[c] * 2.0 * kPi / p * K, Vt);
                 for (int ia = 0; ia < nac; ia++) {
                     int e[3];
@@ -535,7 +531,7 @@ __global__ void grad_1e_kernel(Pairs P, Shells S, BasisPrimDev B, AtomsDev At, R
                     PC2 += PC[x] * PC[x];
                 }
                 double F[NM1];
-                boys_eval_n(la + 1 + lb, p * PC2, boys, F);
+                boys_eval_n(la + 1 + lb, p * PC2, boys, 1.0, F);
                 double Vt[NM1 * NA1 * NB1];
                 os_nuclear(la + 1, lb, p, PA, PB, PC, F, -At.Z[c] * 2.0 * kPi / p * K, Vt);
                 for (int lev = 0; lev < 2; lev++) {
@@ -615,7 +611,7 @@ __global__ void boys_eval_kernel(int n, int m, const double* T, double* F, const
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double f[BOYS_MMAX + 1];
-    boys_eval_n(m, T[i], boys, f);
+    boys_eval_n(m, T[i], boys, 1.0, f);
     F[i] = f[m];
 }
 
@@ -656,33 +652,64 @@ void launch_boys_eval(int n, int m, const double* T, double* F, const double* bo
 }
 
 // F_m(T) = e^{-T} sum_i (2T)^i / ((2m+1)(2m+3)...(2m+2i+1)), a sum of positive
-// terms evaluated in long double.
+// terms evaluated in long double; stored as F_{m+j}(T_k) / j! and e^{-T_k}.
 void boys_fill_table(double* tab)
 {
+    const int NM = BOYS_MT + BOYS_NTAYLOR;
+    long double F[BOYS_MT + BOYS_NTAYLOR];
     for (int k = 0; k < BOYS_NT; k++) {
         const long double T = (long double)k / BOYS_GRID;
-        for (int m = 0; m < BOYS_NM; m++) {
+        for (int m = 0; m < NM; m++) {
             long double term = 1.0L / (2 * m + 1), sum = term;
             for (int i = 1; i < 2000; i++) {
                 term *= 2.0L * T / (2 * m + 2 * i + 1);
                 sum += term;
                 if (term < 1e-22L * sum) break;
             }
-            tab[k * BOYS_NM + m] = (double)(expl(-T) * sum);
+            F[m] = expl(-T) * sum;
         }
+        long double fact = 1.0L;
+        for (int j = 0; j < BOYS_NTAYLOR; j++) {
+            if (j > 0) fact *= j;
+            for (int m = 0; m < BOYS_MT; m++)
+                tab[((size_t)k * BOYS_MT + m) * BOYS_NTAYLOR + j] = (double)(F[m + j] / fact);
+        }
+        tab[(size_t)BOYS_NT * BOYS_MT * BOYS_NTAYLOR + k] = (double)expl(-T);
     }
 }
 
-void boys_table_upload(double** dev_tab)
+void boys_table_upload(double** dev_tab, float** dev_tabf)
 {
-    static double host[BOYS_NT * BOYS_NM];
+    static double host[BOYS_TAB_DOUBLES];
+    static float hostf[BOYS_TAB_FLOATS];
     static bool filled = false;
     if (!filled) {
         boys_fill_table(host);
+        for (int k = 0; k < BOYS_NT; k++) {
+            for (int m = 0; m < BOYS_MT; m++)
+                for (int j = 0; j < BOYS_NTAYLOR_F; j++)
+                    hostf[((size_t)k * BOYS_MT + m) * BOYS_NTAYLOR_F + j] =
+                        (float)host[((size_t)k * BOYS_MT + m) * BOYS_NTAYLOR + j];
+            hostf[(size_t)BOYS_NT * BOYS_MT * BOYS_NTAYLOR_F + k] = (float)host[(size_t)BOYS_NT * BOYS_MT * BOYS_NTAYLOR + k];
+        }
         filled = true;
     }
     cudaMalloc(dev_tab, sizeof(host));
     cudaMemcpy(*dev_tab, host, sizeof(host), cudaMemcpyHostToDevice);
+    cudaMalloc(dev_tabf, sizeof(hostf));
+    cudaMemcpy(*dev_tabf, hostf, sizeof(hostf), cudaMemcpyHostToDevice);
+}
+
+__global__ void to_float_kernel(const double* src, float* dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+void launch_to_float(const double* src, float* dst, long long n, cudaStream_t st)
+{
+    if (n <= 0) return;
+    to_float_kernel<<<256, 256, 0, st>>>(src, dst, n);
 }
 
 }  // namespace pimd

@@ -23,15 +23,19 @@ __host__ __device__ constexpr int cart_index(int lx, int ly, int lz)
     return (lx + ly + lz - lx) * (lx + ly + lz - lx + 1) / 2 + lz;
 }
 
-// primitive-pair fields, stored SoA: pp[((f * PIMD_MAXPP) + k) * npair + g]
+// primitive-pair fields, stored SoA: pp[((f * PIMD_MAXPP) + k) * npair + g];
+// the first PP_NERI are what the Fock-build primitive loop reads
 enum PPField {
-    PP_P = 0,   // p = a + b
-    PP_IP,      // 1 / p
+    PP_P = 0,             // p = a + b
     PP_PX, PP_PY, PP_PZ,  // Gaussian product centre P
-    PP_K,       // sqrt(2) pi^{5/4} c_a c_b exp(-ab/p |AB|^2) / p
+    PP_K,                 // sqrt(2) pi^{5/4} c_a c_b exp(-ab/p |AB|^2) / p
+    PP_PAX, PP_PAY, PP_PAZ,  // P - A
+    PP_O2P,               // 1 / (2p)
+    PP_O2PP,              // 1 / (2p^2)
     PP_EA, PP_EB,         // exponents a, b (gradient weights)
     PP_NF
 };
+constexpr int PP_NERI = PP_EA;
 
 struct Shells {           // all replicas concatenated
     const double* xyz;    // [nshell][3] centre (bohr)
@@ -48,6 +52,7 @@ struct Pairs {
     const int* npp;       // primitive pairs kept
     const double* pp;     // SoA primitive-pair data
     const double* Q;      // Schwarz factor sqrt(max |(ab|ab)|)
+    const float* ppf;     // FP32 copy of pp (mixed-precision quartets)
 };
 
 struct Reps {

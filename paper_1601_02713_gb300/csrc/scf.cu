@@ -85,6 +85,7 @@ struct pimd_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     double* boys = nullptr;
+    float* boysf = nullptr;
     std::map<std::string, DevBuf> bufs;
     std::string last_error;
     pimd_stats stats{};
@@ -185,7 +186,7 @@ extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
         delete ctx;
         return PIMD_ECUDA;
     }
-    boys_table_upload(&ctx->boys);
+    boys_table_upload(&ctx->boys, &ctx->boysf);
     grad2e_tapes_upload();
     for (int i = 0; i < 8; i++) cudaEventCreate(&ctx->ev[i]);
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
@@ -207,6 +208,7 @@ extern "C" void pimd_ctx_destroy(pimd_ctx* ctx)
     for (auto& m : ctx->mo)
         if (m.C.p) cudaFree(m.C.p);
     if (ctx->boys) cudaFree(ctx->boys);
+    if (ctx->boysf) cudaFree(ctx->boysf);
     for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -325,7 +327,8 @@ struct Batch {
     int maxsh = 0;
     double* Dsh = nullptr;
     std::vector<int> npp;
-    unsigned long long* cnt = nullptr;   // [2 * class pairs]: executed quartets, primitive quartets
+    unsigned long long* cnt = nullptr;   // [4 * class pairs]: executed FP64 quartets and primitive
+                                         // quartets, then the same for FP32
     // pairs grouped by (rep, class)
     std::vector<int> pa, pb;
     std::vector<int> grp0;   // [nrep * 6 + 1] start of group (rep, X)
@@ -396,6 +399,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
             atom_rep.push_back(r);
         }
         if (nel % 2) return set_err(ctx, PIMD_EINVAL, "odd electron count (RHF needs a closed shell)");
+        if (nbf > 768) return set_err(ctx, PIMD_EINVAL, "more than 768 basis functions in one replica");
         bt.nbf[r] = nbf;
         bt.nocc[r] = nel / 2;
         if (bt.nocc[r] > nbf) return set_err(ctx, PIMD_EINVAL, "more occupied orbitals than basis functions");
@@ -487,8 +491,8 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     UPLOAD("nsh_rep", bt.nsh_rep, d_nshr);
     UPLOAD("dsoff", bt.dsoff, d_dsoff);
     ENSURE("Dsh", dso, bt.Dsh);
-    ENSURE("cnt", 2 * 64, bt.cnt);
-    CK(cudaMemsetAsync(bt.cnt, 0, sizeof(unsigned long long) * 2 * 64, ctx->stream));
+    ENSURE("cnt", 4 * 64, bt.cnt);
+    CK(cudaMemsetAsync(bt.cnt, 0, sizeof(unsigned long long) * 4 * 64, ctx->stream));
     bt.R = Reps{d_nbf, d_moff, d_active, d_sh0, d_nshr, d_dsoff};
 
     // pair data, Schwarz factors (unsorted), then sort each group by Q
@@ -499,7 +503,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     ENSURE("npp", npair, d_npp);
     ENSURE("pp", (size_t)PP_NF * PIMD_MAXPP * npair, d_pp);
     ENSURE("Q", npair, d_Q);
-    bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q};
+    bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, nullptr};
     launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
     ctx->stats.kernel_launches += 2;
     for (int X = 0; X < 6; X++) {
@@ -515,37 +519,49 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     }
     CK(cudaGetLastError());
     std::vector<double> Q(npair);
-    if (npair) CK(cudaMemcpyAsync(Q.data(), d_Q, sizeof(double) * npair, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<int> npp(npair);
+    if (npair) {
+        CK(cudaMemcpyAsync(Q.data(), d_Q, sizeof(double) * npair, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(npp.data(), d_npp, sizeof(int) * npair, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     for (int q = 0; q < npair; q++)
         if (!isfinite(Q[q])) return set_err(ctx, PIMD_EINVAL, "non-finite integrals (check coordinates)");
     {
+        // each (replica, class) group ordered by primitive-pair count, then by
+        // Schwarz factor (descending): ket pairs of a warp then run the same
+        // number of primitive iterations, and each equal-count run is sorted by Q
         std::vector<int> perm(npair);
         for (int i = 0; i < npair; i++) perm[i] = i;
         for (size_t g = 0; g + 1 < bt.grp0.size(); g++)
-            std::stable_sort(perm.begin() + bt.grp0[g], perm.begin() + bt.grp0[g + 1],
-                             [&](int x, int y) { return Q[x] > Q[y]; });
-        std::vector<int> pa2(npair), pb2(npair);
+            std::stable_sort(perm.begin() + bt.grp0[g], perm.begin() + bt.grp0[g + 1], [&](int x, int y) {
+                return npp[x] != npp[y] ? npp[x] > npp[y] : Q[x] > Q[y];
+            });
+        std::vector<int> pa2(npair), pb2(npair), npp2(npair);
         std::vector<double> Q2(npair);
         for (int i = 0; i < npair; i++) {
             pa2[i] = bt.pa[perm[i]];
             pb2[i] = bt.pb[perm[i]];
             Q2[i] = Q[perm[i]];
+            npp2[i] = npp[perm[i]];
         }
         bt.pa.swap(pa2);
         bt.pb.swap(pb2);
         Q.swap(Q2);
+        bt.npp.swap(npp2);
         UPLOAD("pa", bt.pa, d_pa);
         UPLOAD("pb", bt.pb, d_pb);
         UPLOAD("Q", Q, d_Q);
-        bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q};
+        float* d_ppf;
+        ENSURE("ppf", (size_t)PP_NF * PIMD_MAXPP * npair, d_ppf);
+        bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, d_ppf};
         launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
-        bt.npp.resize(npair);
-        if (npair) CK(cudaMemcpyAsync(bt.npp.data(), d_npp, sizeof(int) * npair, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        launch_to_float(d_pp, d_ppf, (long long)PP_NF * PIMD_MAXPP * npair, ctx->stream);
     }
-    // quartet tiles: for bra pair i of class X and ket class Y <= X, the ket
-    // pairs with Q_j >= tau / Q_i form a prefix of the sorted group.
+    // quartet tiles: for bra pair i of class X and each run of ket pairs of
+    // class Y <= X with equal primitive count, the ket pairs with
+    // Q_j >= tau / Q_i form a prefix of the run; for X == Y only kets at or
+    // before i are canonical (ab >= cd).
     const int ncp = n_class_pairs();
     bt.tiles.assign(ncp, {});
     bt.nq_cp.assign(ncp, 0);
@@ -563,29 +579,26 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
                 for (int i = b0; i < b1; i++) {
                     if (Q[i] <= 0.0) continue;
                     const double thr = tau / Q[i];
-                    // first index in [k0, k1) with Q < thr (Q descending)
-                    int lo = k0, hi = k1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) / 2;
-                        if (Q[mid] >= thr) lo = mid + 1;
-                        else hi = mid;
+                    for (int s0 = k0; s0 < k1;) {
+                        int s1 = s0;
+                        while (s1 < k1 && bt.npp[s1] == bt.npp[s0]) s1++;
+                        // first index in [s0, s1) with Q < thr (Q descending within the run)
+                        int lo = s0, hi = s1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) / 2;
+                            if (Q[mid] >= thr) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        int kend = lo;
+                        if (X == Y) kend = std::min(kend, i + 1);
+                        if (kend > s0) {
+                            const long long nqi = kend - s0;
+                            bt.nq_cp[cp] += nqi;
+                            bt.nquart_rep[r] += nqi;
+                            for (int c = s0; c < kend; c += 128) tl.push_back(Tile{i, c, std::min(c + 128, kend), r});
+                        }
+                        s0 = s1;
                     }
-                    int kend = lo;
-                    if (X == Y) kend = std::min(kend, i + 1);
-                    if (kend <= k0) continue;
-                    const long long nqi = kend - k0;
-                    bt.nq_cp[cp] += nqi;
-                    bt.nquart_rep[r] += nqi;
-                    const double npp_i = (double)bt.npp[i];
-                    double npp_k = 0.0;
-                    for (int k = k0; k < kend; k++) npp_k += (double)bt.npp[k];
-                    bt.vrr_flops += npp_i * npp_k * (double)class_vrr_flops(cp);
-                    {
-                        int la, lb, lc, ld;
-                        class_pair_ls(cp, &la, &lb, &lc, &ld);
-                        bt.eris += (double)nqi * nsph(la) * nsph(lb) * nsph(lc) * nsph(ld);
-                    }
-                    for (int c = k0; c < kend; c += 128) tl.push_back(Tile{i, c, std::min(c + 128, kend), r});
                 }
             }
             bt.nquart += bt.nq_cp[cp];
@@ -728,16 +741,23 @@ static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, co
 }
 
 // G' += G'(M) over all class pairs for the replicas in the active mask, with
-// the quartets screened by Q_ab Q_cd max|M block| >= tau
-static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, const double* M)
+// the quartets screened by Q_ab Q_cd max|M block| >= tau; those below fp32_tau
+// (if > 0) are evaluated in FP32 from Mf, an FP32 copy of M made here
+static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32_tau, const double* M)
 {
     launch_shell_bounds(bt.S, bt.R, bt.nrep, bt.maxsh, M, bt.Dsh, bt.R.active, ctx->stream);
     ctx->stats.kernel_launches++;
+    float* Mf = nullptr;
+    if (fp32_tau > tau) {
+        ENSURE("Mf", bt.mtot, Mf);
+        launch_to_float(M, Mf, bt.mtot, ctx->stream);
+        ctx->stats.kernel_launches++;
+    }
     for (int cp = 0; cp < n_class_pairs(); cp++) {
         if (bt.tiles[cp].empty()) continue;
-        launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), M, m.G, ctx->boys, tau, bt.Dsh,
-                  bt.cnt + 2 * cp, ctx->stream);
-        ctx->stats.kernel_launches++;
+        launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), M, Mf, m.G, ctx->boys, ctx->boysf,
+                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->stream);
+        ctx->stats.kernel_launches += fp32_tau > tau ? 2 : 1;
     }
     return PIMD_OK;
 }
@@ -822,7 +842,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         UPLOAD("mode", mode, d_mode);
         CK(cudaEventRecord(ctx->ev[2], ctx->stream));
         launch_delta_density(m.rm, nrep, m.D, m.Dp, m.dD, m.G, d_mode, ctx->stream);
-        if ((rc = fock_build(ctx, bt, m, o->schwarz_tau, m.dD))) return rc;
+        if ((rc = fock_build(ctx, bt, m, o->schwarz_tau, o->fp32_tau, m.dD))) return rc;
         CK(cudaEventRecord(ctx->ev[3], ctx->stream));
         ctx->stats.kernel_launches++;
         ctx->stats.fock_builds++;
@@ -963,18 +983,26 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     ctx->stats.nquartets_total = bt.nquart;
     {
         // executed work of all Fock builds of the call, from the device counters
-        std::vector<unsigned long long> cnt(2 * 64);
+        std::vector<unsigned long long> cnt(4 * 64);
         CK(cudaMemcpy(cnt.data(), bt.cnt, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
-        double fl = 0.0, er = 0.0;
+        double fl = 0.0, er = 0.0, fl32 = 0.0;
+        long long q64 = 0, q32 = 0;
         for (int cp = 0; cp < n_class_pairs(); cp++) {
             int la, lb, lc, ld;
             class_pair_ls(cp, &la, &lb, &lc, &ld);
-            fl += (double)cnt[2 * cp + 1] * class_vrr_flops(cp);
-            er += (double)cnt[2 * cp] * nsph(la) * nsph(lb) * nsph(lc) * nsph(ld);
+            const double nfun = (double)nsph(la) * nsph(lb) * nsph(lc) * nsph(ld);
+            fl += (double)cnt[4 * cp + 1] * class_vrr_flops(cp);
+            fl32 += (double)cnt[4 * cp + 3] * class_vrr_flops(cp);
+            er += (double)(cnt[4 * cp] + cnt[4 * cp + 2]) * nfun;
+            q64 += (long long)cnt[4 * cp];
+            q32 += (long long)cnt[4 * cp + 2];
         }
         const int nb = std::max(1, ctx->stats.fock_builds);
         ctx->stats.eri_flops_per_build = fl / nb;
+        ctx->stats.eri_flops32_per_build = fl32 / nb;
         ctx->stats.eris_per_build = er / nb;
+        ctx->stats.quartets_fp64 = q64;
+        ctx->stats.quartets_fp32 = q32;
     }
     bool allconv = true;
     for (int r = 0; r < nrep; r++) {
@@ -1103,7 +1131,7 @@ extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
     bt.R.active = m.active;
     CK(cudaMemcpyAsync(m.D, D_dev, sizeof(double) * bt.mtot, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream));
-    if ((rc = fock_build(ctx, bt, m, schwarz_tau, m.D))) return rc;
+    if ((rc = fock_build(ctx, bt, m, schwarz_tau, 0.0, m.D))) return rc;
     // G_out = G' + G'^T
     CK(cudaMemsetAsync(m.H, 0, sizeof(double) * bt.mtot, ctx->stream));
     launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, nullptr, ctx->stream);
@@ -1152,7 +1180,7 @@ extern "C" int pimd_boys_dev(pimd_ctx* ctx, int n, int mord, const double* T_dev
 extern "C" int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev,
                              void* stream)
 {
-    if (!ctx || nmat <= 0 || n <= 0 || !A_dev || !V_dev || !evals_dev) return PIMD_EINVAL;
+    if (!ctx || nmat <= 0 || n <= 0 || n > 768 || !A_dev || !V_dev || !evals_dev) return PIMD_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
     if (stream) CK(cudaStreamSynchronize((cudaStream_t)stream));
     std::vector<RepMat> rm(nmat);

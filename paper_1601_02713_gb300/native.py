@@ -33,7 +33,8 @@ class PimdStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("fock_builds", ctypes.c_int),
                 ("ms_fock", ctypes.c_double), ("ms_grad2e", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("nquartets_total", ctypes.c_longlong), ("eri_flops_per_build", ctypes.c_double),
-                ("eris_per_build", ctypes.c_double)]
+                ("eris_per_build", ctypes.c_double), ("eri_flops32_per_build", ctypes.c_double),
+                ("quartets_fp64", ctypes.c_longlong), ("quartets_fp32", ctypes.c_longlong)]
 
 
 class PimdError(RuntimeError):

@@ -177,3 +177,51 @@ def test_mo_reuse_guess_matches_core_guess(ctx):
         assert np.abs(G1 - G0).max() < 1e-7
         if s > 0:
             assert np.mean(it1) <= np.mean(it0)
+
+
+def test_mixed_precision_fp32_quartets(ctx, spd):
+    """Quartets whose bound Q_ab Q_cd max|dD| is below 1e-6 run in FP32: the
+    mixed path's bar is 1e-6 Eh and 1e-5 Eh/bohr against the oracle; it must
+    actually route quartets to FP32 and stay close to the FP64 path."""
+    bas, B = spd
+    reps, _ = inputs.workload("water2_min_4beads", nrep=2)
+    Z, Xs = reps.stacked()
+    E64, G64, _, rc = native.pimd_bo_forces(ctx, B, Z, Xs)
+    assert rc == 0
+    E32, G32, info, rc = native.pimd_bo_forces(ctx, B, Z, Xs, native.scf_opts(fp32_tau=1e-6))
+    assert rc == 0
+    st = native.pimd_last_stats(ctx)
+    assert st["quartets_fp32"] > 0
+    assert np.abs(E32 - E64).max() < 1e-7
+    assert np.abs(G32 - G64).max() < 1e-6
+    for k in range(len(Xs)):
+        E0, G0 = _oracle_eg(bas, Z, Xs[k])
+        assert abs(E32[k] - E0) < 1e-6
+        assert np.abs(G32[k] - G0).max() < 1e-5
+
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    return json.load(open(path))
+
+
+@pytest.mark.parametrize("fp32_tau", [0.0, 1e-6])
+def test_water8_full_size_against_stored_oracle(ctx, spd, fp32_tau):
+    """(H2O)8, 192 functions: the first bead of the benchmark workload, in the
+    batched launch of 4 beads the benchmark uses, against the oracle's energy
+    and gradient stored by tests/golden/make_golden.py."""
+    bas, B = spd
+    g = _golden("water8_spd_32beads_rep0.json")
+    reps, _ = inputs.workload("water8_spd_32beads", nrep=4)
+    Z, Xs = reps.stacked()
+    assert np.abs(Xs[0] - np.array(g["coords_bohr"])).max() < 1e-12
+    E, G, info, rc = native.pimd_bo_forces(ctx, B, Z, Xs, native.scf_opts(fp32_tau=fp32_tau))
+    assert rc == 0
+    etol, gtol = (E_TOL, G_TOL) if fp32_tau == 0 else (1e-6, 1e-5)
+    assert abs(E[0] - g["energy"]) < etol, E[0] - g["energy"]
+    assert np.abs(G[0] - np.array(g["gradient"])).max() < gtol
+    assert np.abs(G.sum(axis=1)).max() < 1e-8
