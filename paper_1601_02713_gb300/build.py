@@ -157,20 +157,22 @@ def generate_sources():
         gl.append("namespace pimd {")
         if not heavy[nm]:
             gl += [f"void grad2e_upload_{nm}() {{}}",
-                   f"size_t grad2e_scratch_{nm}(int) {{ return 0; }}",
                    f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                   "                        const double* D, double* grad, const double* boys, double tau, double*, int,",
-                   "                        const double* Dsh, cudaStream_t st)",
+                   "                        const double* D, double* grad, const double* boys, const float* boysf,",
+                   "                        double tau, double fp32_tau, const double* Dsh, cudaStream_t st)",
                    "{",
-                   f"    if (ntiles > 0) grad2e_kernel<GCls_{nm}><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boys, tau, Dsh);",
+                   "    if (ntiles <= 0) return;",
+                   "    const double split = fp32_tau > tau ? fp32_tau : tau;",
+                   f"    grad2e_kernel<GCls_{nm}, double><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boys, split, 1e300, Dsh);",
+                   "    if (fp32_tau > tau)",
+                   f"        grad2e_kernel<GCls_{nm}, float><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boysf, tau, fp32_tau, Dsh);",
                    "}"]
         else:
             gl += _coop_upload_code(nm, True, g)
             gl += [f"void grad2e_upload_{nm}() {{ CoopTape t; int W; size_t b; coop_tape_{nm}(t, W, b); }}",
-                   f"size_t grad2e_scratch_{nm}(int) {{ return 0; }}",
                    f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                   "                        const double* D, double* grad, const double* boys, double tau, double*, int,",
-                   "                        const double* Dsh, cudaStream_t st)",
+                   "                        const double* D, double* grad, const double* boys, const float*, double tau,",
+                   "                        double, const double* Dsh, cudaStream_t st)",
                    "{",
                    "    CoopTape t; int W; size_t bytes;",
                    f"    coop_tape_{nm}(t, W, bytes);",
@@ -187,13 +189,12 @@ def generate_sources():
               "const double*, const float*, double, double, const double*, unsigned long long*, cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-             "double, double*, int, const double*, cudaStream_t")
+             "const float*, double, double, const double*, cudaStream_t")
     for c, nm in zip(classes, names):
         d.append(f"void launch_jk_{nm}({sig_jk});")
         if (c[0], c[1]) == (c[2], c[3]):
             d.append(f"void launch_schwarz_{nm}({sig_sw});")
         d.append(f"void launch_grad2e_{nm}({sig_g});")
-        d.append(f"size_t grad2e_scratch_{nm}(int);")
         d.append(f"void grad2e_upload_{nm}();")
     d.append(f"int n_class_pairs() {{ return {len(classes)}; }}")
     d.append("void class_pair_ls(int cp, int* la, int* lb, int* lc, int* ld)")
@@ -226,13 +227,11 @@ def generate_sources():
     d.append("{ sw_tab[X](P, S, list, n, boys, Q, st); }")
     d.append(f"typedef void (*GFn)({sig_g});")
     d.append("static const GFn g_tab[] = {" + ", ".join(f"launch_grad2e_{nm}" for nm in names) + "};")
-    d.append("typedef size_t (*GsFn)(int);")
-    d.append("static const GsFn gs_tab[] = {" + ", ".join(f"grad2e_scratch_{nm}" for nm in names) + "};")
-    d.append("size_t grad2e_scratch_bytes(int cp, int threads) { return gs_tab[cp](threads); }")
+
     d.append("void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
-             "const double* D, double* grad, const double* boys, double tau, double* scratch, int grid_blocks, "
+             "const double* D, double* grad, const double* boys, const float* boysf, double tau, double fp32_tau, "
              "const double* Dsh, cudaStream_t st)")
-    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, tau, scratch, grid_blocks, Dsh, st); }")
+    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, st); }")
     d.append("void grad2e_tapes_upload() {")
     for nm in names:
         d.append(f"    grad2e_upload_{nm}();")

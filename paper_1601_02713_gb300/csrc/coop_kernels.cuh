@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
         }
         for (int p = 0; p < 3; p++)
             for (int x = 0; x < 3; x++) gX[p][x] = warp_sum_d(gX[p][x]);
-        if (lane == 0) scatter_grad(grad, S, sa, sb, sc, sd, gX[0], gX[1], gX[2]);
+        if (lane == 0) scatter_grad<double>(grad, S, sa, sb, sc, sd, gX[0], gX[1], gX[2]);
         __syncwarp();
     }
 }

@@ -40,9 +40,9 @@ __device__ __forceinline__ int cidx(int lx, int ly, int lz)
 }
 
 // Gamma of one quartet in Cartesian components: Gc[((a*nb+b)*nc+c)*nd+d]
-template <int LA, int LB, int LC, int LD>
+template <int LA, int LB, int LC, int LD, typename R = double>
 __device__ __forceinline__ void gamma_cart(double f, int fa, int fb, int fc, int fd, int N,
-                                           const double* __restrict__ D, double* Gc, double* tmp)
+                                           const double* __restrict__ D, R* Gc, R* tmp)
 {
     constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
     for (int a = 0; a < na; a++)
@@ -55,7 +55,7 @@ __device__ __forceinline__ void gamma_cart(double f, int fa, int fb, int fc, int
                     const double dcd = __ldg(D + (size_t)(fc + c) * N + fd + d);
                     const double dbd = __ldg(D + (size_t)(fb + b) * N + fd + d);
                     const double dad = __ldg(D + (size_t)(fa + a) * N + fd + d);
-                    Gc[((a * nb + b) * nc + c) * nd + d] = f * (4.0 * dab * dcd - dac * dbd - dad * dbc);
+                    Gc[((a * nb + b) * nc + c) * nd + d] = R(f * (4.0 * dab * dcd - dac * dbd - dad * dbc));
                 }
             }
         }
@@ -64,8 +64,8 @@ __device__ __forceinline__ void gamma_cart(double f, int fa, int fb, int fc, int
 
 // sum_{abcd} Gc * d(ab|cd)/dX_i for X at position POS (0: A, 1: B, 2: C), given
 // accessors for the raised (l+1) and lowered (l-1) blocks of that position.
-template <int LA, int LB, int LC, int LD, int POS, class Up, class Dn>
-__device__ __forceinline__ void contract_deriv(const double* Gc, Up up, Dn dn, double g[3])
+template <int LA, int LB, int LC, int LD, int POS, class Up, class Dn, typename R = double>
+__device__ __forceinline__ void contract_deriv(const R* Gc, Up up, Dn dn, R g[3])
 {
     constexpr int L[4] = {LA, LB, LC, LD};
     constexpr int n[4] = {ncart(LA), ncart(LB), ncart(LC), ncart(LD)};
@@ -73,12 +73,12 @@ __device__ __forceinline__ void contract_deriv(const double* Gc, Up up, Dn dn, d
     int ndn[4] = {n[0], n[1], n[2], n[3]};
     nu[POS] = ncart(L[POS] + 1);
     ndn[POS] = L[POS] > 0 ? ncart(L[POS] - 1) : 1;
-    g[0] = g[1] = g[2] = 0.0;
+    g[0] = g[1] = g[2] = R(0);
     for (int i0 = 0; i0 < n[0]; i0++)
         for (int i1 = 0; i1 < n[1]; i1++)
             for (int i2 = 0; i2 < n[2]; i2++)
                 for (int i3 = 0; i3 < n[3]; i3++) {
-                    const double gm = Gc[((i0 * n[1] + i1) * n[2] + i2) * n[3] + i3];
+                    const R gm = Gc[((i0 * n[1] + i1) * n[2] + i2) * n[3] + i3];
                     int idx[4] = {i0, i1, i2, i3};
                     int e[3];
                     cart_of(L[POS], idx[POS], e[0], e[1], e[2]);
@@ -88,7 +88,7 @@ __device__ __forceinline__ void contract_deriv(const double* Gc, Up up, Dn dn, d
                         eu[x]++;
                         int ju[4] = {i0, i1, i2, i3};
                         ju[POS] = cidx(eu[0], eu[1], eu[2]);
-                        double v = up(((ju[0] * nu[1] + ju[1]) * nu[2] + ju[2]) * nu[3] + ju[3]);
+                        R v = up(((ju[0] * nu[1] + ju[1]) * nu[2] + ju[2]) * nu[3] + ju[3]);
                         if (e[x] > 0) {
                             int ed[3] = {e[0], e[1], e[2]};
                             ed[x]--;
@@ -101,22 +101,25 @@ __device__ __forceinline__ void contract_deriv(const double* Gc, Up up, Dn dn, d
                 }
 }
 
+template <typename R = double>
 struct ArrAcc {
-    const double* p;
-    __device__ __forceinline__ double operator()(int i) const { return p[i]; }
+    const R* p;
+    __device__ __forceinline__ R operator()(int i) const { return p[i]; }
 };
 
 
+template <typename R>
 __device__ __forceinline__ void scatter_grad(double* grad, const Shells& S, int sa, int sb, int sc, int sd,
-                                             const double gA[3], const double gB[3], const double gC[3])
+                                             const R gA[3], const R gB[3], const R gC[3])
 {
     const int aa = S.atom[sa], ab = S.atom[sb], ac = S.atom[sc], ad = S.atom[sd];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
-        atomicAdd(grad + 3 * aa + x, gA[x]);
-        atomicAdd(grad + 3 * ab + x, gB[x]);
-        atomicAdd(grad + 3 * ac + x, gC[x]);
-        atomicAdd(grad + 3 * ad + x, -(gA[x] + gB[x] + gC[x]));
+        const double a = gA[x], b = gB[x], c = gC[x];
+        atomicAdd(grad + 3 * aa + x, a);
+        atomicAdd(grad + 3 * ab + x, b);
+        atomicAdd(grad + 3 * ac + x, c);
+        atomicAdd(grad + 3 * ad + x, -(a + b + c));
     }
 }
 
@@ -129,26 +132,29 @@ __device__ __forceinline__ double gamma_bound(const Reps& R, const double* Dsh, 
     return 4.0 * j + k1 + k2;
 }
 
-// Straight-line gradient kernel (generated VRR/HRR), blockDim.x == 128.
-template <class G>
-__global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
+// Straight-line gradient kernel (generated VRR/HRR) in precision R for the
+// quartets whose bound Q_ab Q_cd |Gamma| lies in [tau_lo, tau_hi).
+// blockDim.x == 128.
+template <class G, typename R>
+__global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp, const Tile* __restrict__ tiles,
                                                      const double* __restrict__ Dall, double* __restrict__ grad,
-                                                     const double* __restrict__ boys, double tau,
+                                                     const R* __restrict__ boys, double tau_lo, double tau_hi,
                                                      const double* __restrict__ Dsh)
 {
     constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
-    __shared__ double sbra[PP_NF][PIMD_MAXPP];
+    __shared__ R sbra[PP_NF][PIMD_MAXPP];
     const Tile t = tiles[blockIdx.x];
     const int ab = t.ab;
     if (threadIdx.x < PP_NF * PIMD_MAXPP) {
         const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
-        sbra[f][k] = P.pp[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
+        sbra[f][k] = pp_base(P, R(0))[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     }
     __syncthreads();
     const int cd = t.c0 + threadIdx.x;
     if (cd >= t.c1) return;
     const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
-    if (P.Q[ab] * P.Q[cd] * gamma_bound(R, Dsh, t.rep, sa, sb, sc, sd) < tau) return;
+    const double bound = P.Q[ab] * P.Q[cd] * gamma_bound(Rp, Dsh, t.rep, sa, sb, sc, sd);
+    if (bound < tau_lo || bound >= tau_hi) return;
     double A[3], B[3], Cc[3], Dd[3];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
@@ -157,70 +163,71 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps R, 
         Cc[x] = S.xyz[3 * sc + x];
         Dd[x] = S.xyz[3 * sd + x];
     }
-    double accU[G::N_accU], accA[G::N_accA], accB[G::N_accB], accC[G::N_accC];
-    for (int i = 0; i < G::N_accU; i++) accU[i] = 0.0;
-    for (int i = 0; i < G::N_accA; i++) accA[i] = 0.0;
-    for (int i = 0; i < G::N_accB; i++) accB[i] = 0.0;
-    for (int i = 0; i < G::N_accC; i++) accC[i] = 0.0;
+    R accU[G::N_accU], accA[G::N_accA], accB[G::N_accB], accC[G::N_accC];
+    for (int i = 0; i < G::N_accU; i++) accU[i] = R(0);
+    for (int i = 0; i < G::N_accA; i++) accA[i] = R(0);
+    for (int i = 0; i < G::N_accB; i++) accB[i] = R(0);
+    for (int i = 0; i < G::N_accC; i++) accC[i] = R(0);
     const int nbra = P.npp[ab], nket = P.npp[cd];
     for (int j = 0; j < nket; j++) {
-        double ket[PP_NF];
+        R ket[PP_NF];
         load_ppn(P, cd, j, ket, PP_NF);
         for (int i = 0; i < nbra; i++) {
-            double bra[PP_NERI];
+            R bra[PP_NERI];
 #pragma unroll
             for (int f = 0; f < PP_NERI; f++) bra[f] = sbra[f][i];
-            PrimQuartet g;
-            prim_quartet(bra, ket, g);
-            double F[G::L + 1];
+            PrimQ<R> g;
+            prim_quartet<R>(bra, ket, g);
+            R F[G::L + 1];
             boys_eval<G::L>(g.T, boys, g.theta, F);
-            G::template vrr<double>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1],
-                                    g.QC[2], g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, accU,
-                                    accA, accB, accC, 2.0 * sbra[PP_EA][i], 2.0 * sbra[PP_EB][i], 2.0 * ket[PP_EA]);
+            G::template vrr<R>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1], g.QC[2],
+                               g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, accU, accA, accB,
+                               accC, R(2) * sbra[PP_EA][i], R(2) * sbra[PP_EB][i], R(2) * ket[PP_EA]);
         }
     }
-    const double AB0 = A[0] - B[0], AB1 = A[1] - B[1], AB2 = A[2] - B[2];
-    const double CD0 = Cc[0] - Dd[0], CD1 = Cc[1] - Dd[1], CD2 = Cc[2] - Dd[2];
+    const R AB0 = R(A[0] - B[0]), AB1 = R(A[1] - B[1]), AB2 = R(A[2] - B[2]);
+    const R CD0 = R(Cc[0] - Dd[0]), CD1 = R(Cc[1] - Dd[1]), CD2 = R(Cc[2] - Dd[2]);
     constexpr int NC = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
-    double Gc[NC], tmp[NC];
+    R Gc[NC], tmp[NC];
     double f = 1.0;
     if (sa == sb) f *= 0.5;
     if (sc == sd) f *= 0.5;
     if (ab == cd) f *= 0.5;
     const int r = t.rep;
-    gamma_cart<LA, LB, LC, LD>(f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], R.nbf[r], Dall + R.moff[r], Gc, tmp);
-    double gA[3], gB[3], gC[3];
+    gamma_cart<LA, LB, LC, LD, R>(f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], Rp.nbf[r], Dall + Rp.moff[r], Gc,
+                                  tmp);
+    R gA[3], gB[3], gC[3];
     {
-        double up[ncart(LA + 1) * ncart(LB) * ncart(LC) * ncart(LD)];
-        G::template hrrAp<double>(accA, AB0, AB1, AB2, CD0, CD1, CD2, up);
+        R up[ncart(LA + 1) * ncart(LB) * ncart(LC) * ncart(LD)];
+        G::template hrrAp<R>(accA, AB0, AB1, AB2, CD0, CD1, CD2, up);
         if constexpr (LA > 0) {
-            double dn[ncart(LA > 0 ? LA - 1 : 0) * ncart(LB) * ncart(LC) * ncart(LD)];
-            G::template hrrAm<double>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
-            contract_deriv<LA, LB, LC, LD, 0>(Gc, ArrAcc{up}, ArrAcc{dn}, gA);
+            R dn[ncart(LA > 0 ? LA - 1 : 0) * ncart(LB) * ncart(LC) * ncart(LD)];
+            G::template hrrAm<R>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
+            contract_deriv<LA, LB, LC, LD, 0>(Gc, ArrAcc<R>{up}, ArrAcc<R>{dn}, gA);
         } else {
-            contract_deriv<LA, LB, LC, LD, 0>(Gc, ArrAcc{up}, ArrAcc{up}, gA);
+            contract_deriv<LA, LB, LC, LD, 0>(Gc, ArrAcc<R>{up}, ArrAcc<R>{up}, gA);
         }
     }
     {
-        double up[ncart(LA) * ncart(LB + 1) * ncart(LC) * ncart(LD)];
-        G::template hrrBp<double>(accB, AB0, AB1, AB2, CD0, CD1, CD2, up);
+        R up[ncart(LA) * ncart(LB + 1) * ncart(LC) * ncart(LD)];
+        G::template hrrBp<R>(accB, AB0, AB1, AB2, CD0, CD1, CD2, up);
         if constexpr (LB > 0) {
-            double dn[ncart(LA) * ncart(LB > 0 ? LB - 1 : 0) * ncart(LC) * ncart(LD)];
-            G::template hrrBm<double>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
-            contract_deriv<LA, LB, LC, LD, 1>(Gc, ArrAcc{up}, ArrAcc{dn}, gB);
+            R dn[ncart(LA) * ncart(LB > 0 ? LB - 1 : 0) * ncart(LC) * ncart(LD)];
+            G::template hrrBm<R>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
+            contract_deriv<LA, LB, LC, LD, 1>(Gc, ArrAcc<R>{up}, ArrAcc<R>{dn}, gB);
         } else {
-            contract_deriv<LA, LB, LC, LD, 1>(Gc, ArrAcc{up}, ArrAcc{up}, gB);
+            contract_deriv<LA, LB, LC, LD, 1>(Gc, ArrAcc<R>{up}, ArrAcc<R>{up}, gB);
         }
     }
     {
-        double up[ncart(LA) * ncart(LB) * ncart(LC + 1) * ncart(LD)];
-        G::template hrrCp<double>(accC, AB0, AB1, AB2, CD0, CD1, CD2, up);
+        R up[ncart(LA) * ncart(LB) * ncart(LC + 1) * ncart(LD)];
+        G::template hrrCp<R>(accC, AB0, AB1, AB2, CD0, CD1, CD2, up);
         if constexpr (LC > 0) {
-            double dn[ncart(LA) * ncart(LB) * ncart(LC > 0 ? LC - 1 : 0) * ncart(LD)];
-            G::template hrrCm<double>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
-            contract_deriv<LA, LB, LC, LD, 2>(Gc, ArrAcc{up}, ArrAcc{dn}, gC);
+            R dn[ncart(LA) * ncart(LB) * ncart(LC > 0 ? LC - 1 : 0) * ncart(LD)];
+            G::template hrrCm<R>(accU, AB0, AB1, AB2, CD0, CD1, CD2, dn);
+            contract_deriv<LA, LB, LC, LD, 2>(Gc, ArrAcc<R>{up}, ArrAcc<R>{dn}, gC);
         } else {
-            contract_deriv<LA, LB, LC, LD, 2>(Gc, ArrAcc{up}, ArrAcc{up}, gC);
+            contract_deriv<LA, LB, LC, LD, 2>(Gc, ArrAcc<R>{up}, ArrAcc<R>{up}, gC);
         }
     }
     scatter_grad(grad, S, sa, sb, sc, sd, gA, gB, gC);

@@ -53,11 +53,11 @@ void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Til
                double fp32_tau, const double* Dsh, unsigned long long* cnt, cudaStream_t st);
 void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n, const double* boys,
                     double* Q, cudaStream_t st);
-// gradient: returns scratch bytes the tape path needs for class pair cp (0 if straight-line)
-size_t grad2e_scratch_bytes(int cp, int grid_threads);
+// two-electron gradient of class pair cp: quartets with bound Q_ab Q_cd |Gamma|
+// >= max(tau, fp32_tau) in FP64, those in [tau, fp32_tau) in FP32
 void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
-                   const double* D, double* grad, const double* boys, double tau, double* scratch,
-                   int grid_blocks, const double* Dsh, cudaStream_t st);
+                   const double* D, double* grad, const double* boys, const float* boysf, double tau,
+                   double fp32_tau, const double* Dsh, cudaStream_t st);
 void grad2e_tapes_upload();   // once per device
 void boys_table_upload(double** dev_tab, float** dev_tabf);
 // FP32 copies for the mixed-precision quartets

@@ -936,16 +936,11 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         }
         CK(cudaEventRecord(ctx->ev[4], ctx->stream));
         launch_shell_bounds(bt.S, bt.R, nrep, bt.maxsh, m.D, bt.Dsh, nullptr, ctx->stream);
-        const int grid_blocks = ctx->nsm * 4;
-        size_t scr = 0;
-        for (int cp = 0; cp < n_class_pairs(); cp++) scr = std::max(scr, grad2e_scratch_bytes(cp, grid_blocks * 128));
-        double* d_scr = nullptr;
-        if (scr) ENSURE("grad_scratch", scr / sizeof(double) + 1, d_scr);
         for (int cp = 0; cp < n_class_pairs(); cp++) {
             if (bt.tiles[cp].empty()) continue;
             launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_grad, ctx->boys,
-                          o->schwarz_tau * 1e-2, d_scr, grid_blocks, bt.Dsh, ctx->stream);
-            ctx->stats.kernel_launches++;
+                          ctx->boysf, o->schwarz_tau * 1e-2, o->fp32_tau, bt.Dsh, ctx->stream);
+            ctx->stats.kernel_launches += o->fp32_tau > 0 ? 2 : 1;
         }
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
         ctx->stats.kernel_launches += 3;
