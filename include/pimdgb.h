@@ -154,10 +154,11 @@ int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
 /* Testing hooks (same kernels as the forces path):
  * pimd_fock_dev: for nrep replicas of one molecule and a given density
  *   D[nrep][N][N] (device), write G = J - K/2 (device, [nrep][N][N]) with
- *   J_mn = sum D_ls (mn|ls), K_mn = sum D_ls (ml|ns).
+ *   J_mn = sum D_ls (mn|ls), K_mn = sum D_ls (ml|ns) (Schwarz cutoff
+ *   schwarz_tau; quartets below fp32_tau in FP32 when fp32_tau > schwarz_tau).
  * pimd_one_electron: S, T, V matrices of one molecule (host arrays [N][N]). */
 int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords, const pimd_basis* basis,
-                  double schwarz_tau, const double* D_dev, double* G_dev);
+                  double schwarz_tau, double fp32_tau, const double* D_dev, double* G_dev);
 int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coords, const pimd_basis* basis,
                       double* S, double* T, double* V);
 int pimd_boys_dev(pimd_ctx* ctx, int n, int m, const double* T_dev, double* F_dev);

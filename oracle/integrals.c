@@ -861,3 +861,49 @@ double oracle_deriv_list(BASIS_ARGS, int nq, const int *quartets)
     }
     return total;
 }
+
+/* ------------------------------------------------------------------------- */
+/* One block of G = J - K/2 straight from the definitions, for sampled checks  */
+/* of large systems: for shells a, b                                          */
+/*   J_mn = sum_{c,d} sum_{l in c, s in d} D_ls (mn|ls)                        */
+/*   K_mn = sum_{c,d} sum_{l in c, s in d} D_ls (ml|ns)     (m in a, n in b)   */
+/* over every ordered shell pair (c, d), no screening and no symmetry.        */
+/* ------------------------------------------------------------------------- */
+void oracle_g_block(BASIS_ARGS, const double *D, int a, int b, double *out)
+{
+    MAKE_BASIS;
+    int ns = bs.nshell;
+    int *off = malloc(sizeof(int) * (ns + 1));
+    shell_offsets(&bs, off);
+    int N = off[ns];
+    int na = shell_nbf(&bs, a), nb = shell_nbf(&bs, b);
+    double Jb[25] = {0}, Kb[25] = {0};
+#pragma omp parallel
+    {
+        double Jt[25] = {0}, Kt[25] = {0};
+        double blk[BLK];
+#pragma omp for schedule(dynamic)
+        for (int c = 0; c < ns; c++)
+            for (int d = 0; d < ns; d++) {
+                int nc = shell_nbf(&bs, c), nd = shell_nbf(&bs, d);
+                eri_block(&bs, a, b, c, d, blk); /* (ab|cd) */
+                for (int i = 0; i < na; i++)
+                    for (int j = 0; j < nb; j++)
+                        for (int k = 0; k < nc; k++)
+                            for (int m = 0; m < nd; m++)
+                                Jt[i * nb + j] += D[(off[c] + k) * N + off[d] + m] * blk[((i * nb + j) * nc + k) * nd + m];
+                eri_block(&bs, a, c, b, d, blk); /* (ac|bd) */
+                for (int i = 0; i < na; i++)
+                    for (int k = 0; k < nc; k++)
+                        for (int j = 0; j < nb; j++)
+                            for (int m = 0; m < nd; m++)
+                                Kt[i * nb + j] += D[(off[c] + k) * N + off[d] + m] * blk[((i * nc + k) * nb + j) * nd + m];
+            }
+#pragma omp critical
+        {
+            for (int x = 0; x < na * nb; x++) { Jb[x] += Jt[x]; Kb[x] += Kt[x]; }
+        }
+    }
+    for (int x = 0; x < na * nb; x++) out[x] = Jb[x] - 0.5 * Kb[x];
+    free(off);
+}

@@ -68,6 +68,7 @@ def _load():
         lib.oracle_one_electron.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.oracle_grad_1e.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_g_block.argtypes = basis + [dp, ctypes.c_int, ctypes.c_int, dp]
         lib.oracle_eri_list.argtypes = basis + [ctypes.c_int, ip]
         lib.oracle_eri_list.restype = ctypes.c_double
         lib.oracle_deriv_list.argtypes = basis + [ctypes.c_int, ip]
@@ -211,6 +212,15 @@ def grad_1e(ob: OracleBasis, Z, xyz, D, W):
     _load().oracle_grad_1e(*ob.args(), natom, _dp(Zn), _dp(C), _dp(np.ascontiguousarray(D, float)),
                            _dp(np.ascontiguousarray(W, float)), _dp(g))
     return g
+
+
+def g_block(ob: OracleBasis, D, a: int, b: int) -> np.ndarray:
+    """Block of G = J - K/2 for shells a, b from the definitions, summed over
+    every ordered shell pair without screening (sampled checks of large
+    systems)."""
+    out = np.zeros((ob.shell_nbf(a), ob.shell_nbf(b)))
+    _load().oracle_g_block(*ob.args(), _dp(np.ascontiguousarray(D, float)), int(a), int(b), _dp(out))
+    return out
 
 
 def eri_list(ob: OracleBasis, quartets) -> float:

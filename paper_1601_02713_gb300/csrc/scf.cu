@@ -1107,7 +1107,8 @@ extern "C" int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* nato
 // testing hooks
 // ---------------------------------------------------------------------------
 extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
-                             const pimd_basis* basis, double schwarz_tau, const double* D_dev, double* G_dev)
+                             const pimd_basis* basis, double schwarz_tau, double fp32_tau, const double* D_dev,
+                             double* G_dev)
 {
     if (!ctx || !basis || nrep <= 0 || natom <= 0 || !Z || !coords || !D_dev || !G_dev) return PIMD_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
@@ -1126,7 +1127,7 @@ extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
     bt.R.active = m.active;
     CK(cudaMemcpyAsync(m.D, D_dev, sizeof(double) * bt.mtot, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream));
-    if ((rc = fock_build(ctx, bt, m, schwarz_tau, 0.0, m.D))) return rc;
+    if ((rc = fock_build(ctx, bt, m, schwarz_tau, fp32_tau, m.D))) return rc;
     // G_out = G' + G'^T
     CK(cudaMemsetAsync(m.H, 0, sizeof(double) * bt.mtot, ctx->stream));
     launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, nullptr, ctx->stream);

@@ -78,7 +78,7 @@ def load(path: str | None = None):
     lib.string_images_forces_dev.argtypes = [_P, ctypes.c_int, _I, _I, _P, _P, ctypes.POINTER(PimdScfOpts), _P, _P,
                                              ctypes.POINTER(PimdInfo), _P]
     lib.pimd_last_stats.argtypes = [_P, ctypes.POINTER(PimdStats)]
-    lib.pimd_fock_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.c_double, _P, _P]
+    lib.pimd_fock_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.c_double, ctypes.c_double, _P, _P]
     lib.pimd_one_electron.argtypes = [_P, ctypes.c_int, _I, _D, _P, _D, _D, _D]
     lib.pimd_boys_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
     lib.pimd_peak_bench.argtypes = [ctypes.c_int, _D, _D, _D]
@@ -235,13 +235,15 @@ def string_images_forces_dev(ctx: Context, basis: Basis, natom_of_img, Z_concat,
     return _infos(info), rc
 
 
-def pimd_fock_dev(ctx: Context, basis: Basis, Z, coords, D_dev, G_dev, schwarz_tau: float = 1e-12):
+def pimd_fock_dev(ctx: Context, basis: Basis, Z, coords, D_dev, G_dev, schwarz_tau: float = 1e-12,
+                  fp32_tau: float = 0.0):
     """G = J - K/2 of a given density for nrep replicas (D, G device tensors
     [nrep, N, N]); coords host [nrep, natom, 3]."""
     Z = np.ascontiguousarray(Z, np.int32)
     X = np.ascontiguousarray(coords, np.float64)
     _check(load().pimd_fock_dev(ctx.handle, X.shape[0], X.shape[1], _ip(Z), _dp(X), basis.handle,
-                                float(schwarz_tau), _P(D_dev.data_ptr()), _P(G_dev.data_ptr())), "pimd_fock_dev")
+                                float(schwarz_tau), float(fp32_tau), _P(D_dev.data_ptr()), _P(G_dev.data_ptr())),
+           "pimd_fock_dev")
 
 
 def pimd_one_electron(ctx: Context, basis: Basis, Z, coords):

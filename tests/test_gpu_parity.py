@@ -225,3 +225,35 @@ def test_water8_full_size_against_stored_oracle(ctx, spd, fp32_tau):
     assert abs(E[0] - g["energy"]) < etol, E[0] - g["energy"]
     assert np.abs(G[0] - np.array(g["gradient"])).max() < gtol
     assert np.abs(G.sum(axis=1)).max() < 1e-8
+
+
+@pytest.mark.parametrize("fp32_tau,tol", [(0.0, 1e-8), (1e-6, 1e-7)])
+def test_water32_full_size_sampled_fock_blocks(ctx, spd, fp32_tau, tol):
+    """(H2O)32, 768 functions (the largest workload): the full Fock-build
+    launch for one bead with a seeded density of SCF-like magnitude, checked
+    on sampled shell-pair blocks that the oracle computes from the definition
+    (every ordered shell pair, no screening): s-s on one atom, p-s across the
+    cluster, d-p and d-d blocks."""
+    bas, B = spd
+    reps, _ = inputs.workload("water32_spd_16beads", nrep=1)
+    Z, Xs = reps.stacked()
+    ob = O.OracleBasis.build(bas, Z, Xs[0])
+    N = ob.nbf
+    rng = np.random.default_rng(32)
+    Cocc = rng.normal(size=(N, 160)) / np.sqrt(N)
+    D = 2.0 * Cocc @ Cocc.T
+    Dt = torch.tensor(D[None], device="cuda")
+    Gt = torch.zeros_like(Dt)
+    native.pimd_fock_dev(ctx, B, Z, Xs, Dt, Gt, 1e-12, fp32_tau)
+    G = Gt[0].cpu().numpy()
+    off = np.cumsum([0] + [ob.shell_nbf(s) for s in range(len(ob.l))])
+    ls = np.asarray(ob.l)
+    d_sh = np.nonzero(ls == 2)[0]
+    p_sh = np.nonzero(ls == 1)[0]
+    s_sh = np.nonzero(ls == 0)[0]
+    picks = [(s_sh[0], s_sh[1]), (p_sh[3], s_sh[-5]), (d_sh[7], p_sh[40]), (d_sh[20], d_sh[21])]
+    for a, b in picks:
+        ref = O.g_block(ob, D, int(a), int(b))
+        got = G[off[a]:off[a + 1], off[b]:off[b + 1]]
+        err = np.abs(got - ref).max()
+        assert err < tol * max(1.0, np.abs(ref).max()), (a, b, err)
