@@ -118,6 +118,23 @@ def make_steps(name, nrep, nsteps, rank):
     return seq, kind
 
 
+def max_over_ranks(t_local, dist, device):
+    """Step time of the whole job: the maximum over ranks (every rank waits
+    for the slowest before the next step)."""
+    if dist is None:
+        return t_local
+    import torch
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(beads_per_rank, world, steps, t_max):
+    """Whole-job bead evaluations per second: all ranks' beads over the
+    slowest rank's time (weak scaling: each rank owns its own beads)."""
+    return beads_per_rank * world * steps / t_max
+
+
 # ---------------------------------------------------------------- CPU baseline (oracle)
 def oracle_sample(step_reps, kind, iterations, n_eri, n_der, seed=11):
     """Time the oracle on a bounded sample of one bead of the workload:
@@ -240,12 +257,8 @@ def main():
         assert all(x["converged"] for x in infos)
     clk = clocks.stop()
     t_local = sum(ms) / 1000.0
-    t_max = t_local
-    if dist is not None:
-        tt = torch.tensor([t_local], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = nrep * world * K / t_max
+    t_max = max_over_ranks(t_local, dist, dev)
+    value = job_throughput(nrep, world, K, t_max)
 
     # end to end through the host-buffer entry point (H2D coords, D2H E and G)
     Xh = [seq[i].stacked()[1] for i in range(W + K, W + K + E2E)]
@@ -254,12 +267,8 @@ def main():
     for x in Xh:
         Eh, Gh, info_h, rc = native.pimd_bo_forces(ctx, basis, Z, x, opts)
         assert rc == 0
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = nrep * world * E2E / t_e2e
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = job_throughput(nrep, world, E2E, t_e2e)
 
     # roofline of the dominant kernel (the Fock build: all quartet classes)
     fock_ms = sum(s["ms_fock"] for s in stats)
