@@ -61,7 +61,9 @@ typedef struct {
                              Q_ab Q_cd max|D block| is below it (D: the density increment of an
                              incremental build) are evaluated in FP32 and accumulated in FP64 */
     int guess;            /* 0 core Hamiltonian, 1 previous MOs of the same replica index (Sec. 2:
-                             MOs of each replica reused as the next step's guess), falls back to 0 */
+                             MOs of each replica reused as the next step's guess), falls back to 0;
+                             2 learned density (the model attached by pimd_ctx_set_guess_model);
+                             3 previous MOs where cached, else the learned density */
     int deterministic;    /* reserved, 0 */
     int want_gradient;    /* 1 */
 } pimd_scf_opts;
@@ -189,6 +191,77 @@ int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V
  * capture. All calls share the one workspace: calls that overlap on the GPU
  * (from several host threads or streams) race and give wrong results. */
 int pimd_eigh_noalloc(int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned initial density (no counterpart in the paper, which reuses the
+ * previous step's MOs, Sec. 2): a multilayer perceptron predicts every
+ * atom-pair block of the density matrix, A == B included, from invariant
+ * features of the pair's environment, in a local frame of the pair (e_z along
+ * A -> B, or for A == B towards A's nearest neighbour; e_x from the atom
+ * nearest the midpoint, or A's second-nearest neighbour). Blocks of pairs
+ * more than 4 Angstrom apart are zero. The predicted blocks are rotated to
+ * the lab frame, same-atom blocks symmetrised, and the matrix scaled to
+ * tr(D S) = number of electrons; the SCF's first Fock build and
+ * diagonalisation then make it idempotent. It changes the number of SCF
+ * iterations, never the converged result. Elements H, C and O only, at most
+ * 14 basis functions and 8 shells per atom.
+ * Network: 96 features -> 3 hidden layers of 256 (SiLU) -> one linear head
+ * per pair type (the same atom H, C or O; the element pairs OO, OC, OH, CC,
+ * CH, HH), head width = the block size. BF16 tensor-core GEMMs with FP32
+ * accumulation, FP32 master weights, Adam. Everything runs on the device of
+ * the current CUDA device at creation.
+ */
+typedef struct pimd_guess pimd_guess;
+
+/* Create a model for the basis (its per-element shells fix the head sizes);
+ * weights initialised from `seed` (Glorot uniform). */
+int pimd_guess_create(pimd_guess** out, const pimd_basis* basis, unsigned long long seed);
+void pimd_guess_destroy(pimd_guess* g);
+/* Number of parameters (weights and biases, in the layout of pimd_guess_mlp_grad). */
+long long pimd_guess_nparam(const pimd_guess* g);
+/* Converge the SCF of nrep replicas of one molecule (arguments as for
+ * pimd_bo_forces; the gradient is not computed) and add every replica's
+ * converged density blocks, in the local frames, with the pairs' features to
+ * the model's training set (held on the device). info[nrep] may be NULL. */
+int pimd_guess_add_data(pimd_guess* g, pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
+                        const pimd_basis* basis, const pimd_scf_opts* opts, pimd_info* info);
+/* Replicas in the training set. */
+long long pimd_guess_ndata(const pimd_guess* g);
+void pimd_guess_clear_data(pimd_guess* g);
+/* `epochs` passes of Adam (learning rate lr) over the training set, one step
+ * per pimd_guess_add_data call's replicas; loss_history[epochs] (may be NULL)
+ * gets each epoch's mean squared error over the set, weighted per entry. */
+int pimd_guess_train(pimd_guess* g, int epochs, double lr, double* loss_history);
+/* Mean squared error of the current weights over the training set. */
+int pimd_guess_loss(pimd_guess* g, double* loss);
+/* Weights to / from a file (the model's basis must match). */
+int pimd_guess_save(const pimd_guess* g, const char* path);
+int pimd_guess_load(pimd_guess* g, const char* path);
+/* Attach (or with NULL detach) the model used by guess = 2 and 3; the
+ * context does not own it. */
+int pimd_ctx_set_guess_model(pimd_ctx* ctx, pimd_guess* g);
+
+/* Testing hooks of the learned guess (same kernels as above).
+ * pimd_guess_pair_data: the pair rows of one molecule: npair_out, pair_AB
+ *   [npair][2] (A, B atom indices), block_off[npair] (offset of the pair's
+ *   block, row-major nbf_A x nbf_B, in local_out / local_in), feats
+ *   [npair][96] (float), frames [npair][9] (rows e_x, e_y, e_z); if D (host,
+ *   N x N) is given, local_out gets M_A^T D_AB M_B for every pair; if
+ *   local_in is given, D_out (N x N) gets the lab blocks M_A L M_B^T of the
+ *   pairs within the cutoff (same-atom blocks symmetrised first), zero
+ *   elsewhere, unscaled. Arrays sized for npair_max pairs (n(n+1)/2) and
+ *   nout_max block entries.
+ * pimd_guess_mlp_grad: loss (mean over all n x width entries) and gradients
+ *   of the network on given features X[n][96] and targets Y[n][width] of one
+ *   pair type (0..2 the same atom H, C, O; 3..8 the pairs OO, OC, OH, CC, CH,
+ *   HH, heavier element first; width = nbf_A x nbf_B); params_out / grads_out (pimd_guess_nparam floats each, may be
+ *   NULL) get the FP32 weights and the gradient. Layout per layer k (3 hidden,
+ *   then 9 heads): W_k row-major [fan_in][fan_out], then b_k[fan_out]. */
+int pimd_guess_pair_data(pimd_guess* g, int natom, const int* Z, const double* coords, const double* D,
+                         const float* local_in, int npair_max, long long nout_max, int* npair_out, int* pair_AB,
+                         long long* block_off, float* feats, double* frames, float* local_out, double* D_out);
+int pimd_guess_mlp_grad(pimd_guess* g, int n, int type, const float* X, const float* Y, double* loss,
+                        float* params_out, float* grads_out);
 
 /* Roofline denominators measured on the device: FP64 FMA, FP32 FMA and FP64
  * tensor-core MMA throughput in TFLOP/s (bounded microbenchmarks, ~1 s). Any

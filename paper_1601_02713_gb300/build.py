@@ -27,7 +27,7 @@ LIB = os.path.join(BUILD, "libpimdgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills", "-w", "-I" + CSRC, "-I" + GEN, "-I" + INCLUDE]
-HAND_WRITTEN = ["onee.cu", "linalg.cu", "scf.cu", "peaks.cu"]
+HAND_WRITTEN = ["onee.cu", "linalg.cu", "scf.cu", "peaks.cu", "guess.cu"]
 
 
 def nvcc_path():

@@ -3,7 +3,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "pimd_dev.cuh"
+
+struct pimd_basis;
+struct pimd_guess;
 
 namespace pimd {
 
@@ -119,5 +124,21 @@ void launch_shell_bounds(const Shells& S, const Reps& R, int nrep, int maxsh, co
 // mode 2, Dprev <- D; mode 0 replicas untouched
 void launch_delta_density(const RepMat* rm, int nrep, const double* D, double* Dprev, double* dD, double* G,
                           const int* mode, cudaStream_t st);
+
+// ------------------------------------------------------------------ learned guess
+// shells (angular momenta into l_out, at most maxsh) of element Z: count, or -1
+int basis_elem_shells(const pimd_basis* b, int Z, int* l_out, int maxsh);
+// basis functions per atom of element Z in the model's basis, or -1
+int guess_elem_nbf(const pimd_guess* g, int Z);
+int guess_device(const pimd_guess* g);
+// converged densities d_D [rm] of nrep replicas -> a training row set of the model
+int guess_collect_device(pimd_guess* g, int nrep, const int* natom_of, const int* Zc,
+                         const std::vector<int>& atom_f0, const double* d_xyz, const int* d_Z, const int* d_atom0,
+                         const RepMat* d_rm, double* d_D, cudaStream_t st);
+// predicted densities of the replicas in mask (host and device copies) into d_D
+int guess_predict_device(pimd_guess* g, int nrep, const int* natom_of, const int* Zc,
+                         const std::vector<int>& atom_f0, const std::vector<int>& mask, const double* d_xyz,
+                         const int* d_Z, const int* d_atom0, const RepMat* d_rm, const int* d_mask, const double* d_S,
+                         double* d_tmp, long long mtot, double* d_D, cudaStream_t st);
 
 }  // namespace pimd

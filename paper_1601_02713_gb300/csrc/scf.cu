@@ -98,6 +98,7 @@ struct pimd_ctx {
     std::vector<MO> mo;
     cudaEvent_t ev[8];
     int nsm = 152;
+    pimd_guess* guess_model = nullptr;   // not owned (guess = 2, 3)
 };
 
 static int set_err(pimd_ctx* ctx, int code, const std::string& msg)
@@ -223,6 +224,25 @@ extern "C" void pimd_ctx_clear_guess(pimd_ctx* ctx)
     }
 }
 
+extern "C" int pimd_ctx_set_guess_model(pimd_ctx* ctx, pimd_guess* g)
+{
+    if (!ctx) return PIMD_EINVAL;
+    if (g && guess_device(g) != ctx->device) return set_err(ctx, PIMD_EINVAL, "guess model on another device");
+    ctx->guess_model = g;
+    return PIMD_OK;
+}
+
+namespace pimd {
+int basis_elem_shells(const pimd_basis* b, int Z, int* l_out, int maxsh)
+{
+    auto it = b->elem.find(Z);
+    if (it == b->elem.end()) return -1;
+    const auto& sh = b->shells[it->second];
+    for (size_t k = 0; k < sh.size() && (int)k < maxsh; k++) l_out[k] = sh[k].l;
+    return (int)sh.size();
+}
+}  // namespace pimd
+
 extern "C" int pimd_basis_create(pimd_basis** out, int nelem, const int* Z_of_elem, const int* nshell_of_elem,
                                  const int* shell_l, const int* shell_nprim, const double* exps,
                                  const double* coefs, int spherical)
@@ -316,6 +336,8 @@ extern "C" int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out)
 struct Batch {
     int nrep = 0;
     std::vector<int> natom, atom0, nbf, nocc;
+    std::vector<int> atom_f0;   // first function of each atom within its replica
+    int* d_Zi = nullptr;        // nuclear charges (int) on the device
     std::vector<long long> moff;
     long long mtot = 0;
     int maxN = 0;
@@ -384,6 +406,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
             auto it = basis->elem.find(Z);
             if (it == basis->elem.end()) return set_err(ctx, PIMD_EINVAL, "element missing from basis");
             nel += Z;
+            bt.atom_f0.push_back(nbf);
             const int e = it->second;
             for (size_t k = 0; k < basis->shells[e].size(); k++) {
                 const ShellDef& d = basis->shells[e][k];
@@ -440,6 +463,10 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     double* d_Z;
     int *d_atom0, *d_atom_rep;
     UPLOAD("Z", Zd, d_Z);
+    {
+        std::vector<int> Zi(Zc, Zc + a0);
+        UPLOAD("Zi", Zi, bt.d_Zi);
+    }
     UPLOAD("atom0", bt.atom0, d_atom0);
     UPLOAD("atom_rep", atom_rep, d_atom_rep);
     bt.At.xyz = d_xyz;
@@ -804,14 +831,21 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
                 return set_err(ctx, PIMD_EBASIS, "overlap matrix numerically singular");
     }
     launch_orth_from_eig(m.rm, nrep, m.Cp, m.Ev, m.ldE, m.X, ctx->stream);
-    // guess: cached MOs of the same replica index, else the core Hamiltonian
+    // guess per replica: cached MOs of the same replica index (guess 1, 3),
+    // else the learned density (guess 2, 3), else the core Hamiltonian
+    const bool want_cache = o->guess == 1 || o->guess == 3;
+    const bool want_learned = o->guess == 2 || o->guess == 3;
+    if (want_learned && !ctx->guess_model) return set_err(ctx, PIMD_EINVAL, "learned guess without a model");
     if ((int)ctx->mo.size() < nrep) ctx->mo.resize(nrep);
-    std::vector<int> use_cache(nrep, 0), core(nrep, 0);
+    std::vector<int> use_cache(nrep, 0), core(nrep, 0), learned(nrep, 0);
+    int nlearned = 0;
     for (int r = 0; r < nrep; r++) {
         auto& mo = ctx->mo[r];
         std::vector<int> z(Zc + bt.atom0[r], Zc + bt.atom0[r + 1]);
-        use_cache[r] = (o->guess == 1 && mo.N == bt.nbf[r] && mo.Z == z);
-        core[r] = !use_cache[r];
+        use_cache[r] = (want_cache && mo.N == bt.nbf[r] && mo.Z == z);
+        learned[r] = !use_cache[r] && want_learned;
+        core[r] = !use_cache[r] && !learned[r];
+        nlearned += learned[r];
         if (use_cache[r])
             CK(cudaMemcpyAsync(m.C + bt.moff[r], mo.C.p, sizeof(double) * bt.nbf[r] * bt.nbf[r],
                                cudaMemcpyDeviceToDevice, ctx->stream));
@@ -828,6 +862,22 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     launch_copy_mats(m.rm, nrep, m.H, m.Fb, d_mask, ctx->stream);
     diag_density(ctx, bt, m, plan, d_mask);
     gemm(ctx, plan.Dn, d_mc);
+    if (nlearned > 0) {
+        pimd_guess* gm = ctx->guess_model;
+        if (guess_device(gm) != ctx->device) return set_err(ctx, PIMD_EINVAL, "guess model on another device");
+        for (int a = 0; a < bt.atom0[nrep]; a++) {
+            const int e = basis->elem.at(Zc[a]);
+            if (guess_elem_nbf(gm, Zc[a]) != basis->nbf_elem[e])
+                return set_err(ctx, PIMD_EINVAL, "guess model built for another basis or element set");
+        }
+        int* d_ml;
+        UPLOAD("mask_learned", learned, d_ml);
+        // m.dD is scratch until the first incremental-build step overwrites it
+        rc = guess_predict_device(gm, nrep, natom_of, Zc, bt.atom_f0, learned, d_xyz, bt.d_Zi, bt.At.rep_atom0,
+                                  m.rm, d_ml, m.S, m.dD, bt.mtot, m.D, ctx->stream);
+        if (rc) return set_err(ctx, rc, "learned guess failed");
+        ctx->stats.kernel_launches += 19;
+    }
     // SCF iterations
     std::vector<double> E(nrep), emax(nrep), Eprev(nrep, 0.0);
     std::vector<int> iters(nrep, 0), conv(nrep, 0);
@@ -1022,7 +1072,7 @@ static int check_common(pimd_ctx* ctx, const pimd_basis* basis, const pimd_scf_o
         memcpy(&o, opts, opts->struct_size);
     }
     if (!(o.conv_energy > 0) || !(o.conv_error > 0) || o.max_iter < 1 || o.max_iter > 10000 ||
-        !(o.schwarz_tau >= 0))
+        !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 3)
         return set_err(ctx, PIMD_EINVAL, "bad SCF options");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
     return PIMD_OK;
@@ -1062,6 +1112,44 @@ static int forces_impl(pimd_ctx* ctx, int nrep, const int* natom_of, const int* 
     if (o.want_gradient) CK(cudaMemcpyAsync(grad, d_g, sizeof(double) * natot * 3, k, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return rc;
+}
+
+extern "C" int pimd_guess_add_data(pimd_guess* g, pimd_ctx* ctx, int nrep, int natom, const int* Z,
+                                   const double* coords, const pimd_basis* basis, const pimd_scf_opts* opts,
+                                   pimd_info* info)
+{
+    if (!g || !ctx || !basis || nrep <= 0 || natom <= 0 || !Z || !coords) return PIMD_EINVAL;
+    if (guess_device(g) != ctx->device) return set_err(ctx, PIMD_EINVAL, "guess model on another device");
+    std::vector<int> atom_f0;
+    for (int r = 0; r < nrep; r++) {
+        int f = 0;
+        for (int i = 0; i < natom; i++) {
+            auto it = basis->elem.find(Z[i]);
+            if (it == basis->elem.end()) return set_err(ctx, PIMD_EINVAL, "element missing from basis");
+            if (guess_elem_nbf(g, Z[i]) != basis->nbf_elem[it->second])
+                return set_err(ctx, PIMD_EINVAL, "guess model built for another basis or element set");
+            atom_f0.push_back(f);
+            f += basis->nbf_elem[it->second];
+        }
+    }
+    pimd_scf_opts o;
+    pimd_scf_opts_default(&o);
+    if (opts) {
+        if (opts->struct_size < sizeof(size_t) || opts->struct_size > sizeof(pimd_scf_opts)) return PIMD_EINVAL;
+        memcpy(&o, opts, opts->struct_size);
+        o.struct_size = sizeof(pimd_scf_opts);
+    }
+    o.want_gradient = 0;
+    std::vector<int> natom_of(nrep, natom), Zc;
+    for (int r = 0; r < nrep; r++) Zc.insert(Zc.end(), Z, Z + natom);
+    std::vector<double> E(nrep);
+    int rc = forces_impl(ctx, nrep, natom_of.data(), Zc.data(), coords, false, basis, &o, E.data(), nullptr, false,
+                         info, nullptr);
+    if (rc) return rc;   // unconverged densities are not training data
+    // the call's device state: coordinates, charges, replica layout, converged D
+    return guess_collect_device(g, nrep, natom_of.data(), Zc.data(), atom_f0, (const double*)ctx->bufs["xyz"].p,
+                                (const int*)ctx->bufs["Zi"].p, (const int*)ctx->bufs["atom0"].p,
+                                (const RepMat*)ctx->bufs["rm"].p, (double*)ctx->bufs["D"].p, ctx->stream);
 }
 
 extern "C" int pimd_bo_forces(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,

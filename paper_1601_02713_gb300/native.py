@@ -84,6 +84,27 @@ def load(path: str | None = None):
     lib.pimd_peak_bench.argtypes = [ctypes.c_int, _D, _D, _D]
     lib.pimd_eigh_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
     lib.pimd_eigh_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
+    _F = ctypes.POINTER(ctypes.c_float)
+    _LL = ctypes.POINTER(ctypes.c_longlong)
+    lib.pimd_guess_create.argtypes = [ctypes.POINTER(_P), _P, ctypes.c_ulonglong]
+    lib.pimd_guess_destroy.argtypes = [_P]
+    lib.pimd_guess_destroy.restype = None
+    lib.pimd_guess_nparam.argtypes = [_P]
+    lib.pimd_guess_nparam.restype = ctypes.c_longlong
+    lib.pimd_guess_ndata.argtypes = [_P]
+    lib.pimd_guess_ndata.restype = ctypes.c_longlong
+    lib.pimd_guess_clear_data.argtypes = [_P]
+    lib.pimd_guess_clear_data.restype = None
+    lib.pimd_guess_add_data.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.POINTER(PimdScfOpts),
+                                        _P]
+    lib.pimd_guess_train.argtypes = [_P, ctypes.c_int, ctypes.c_double, _D]
+    lib.pimd_guess_loss.argtypes = [_P, _D]
+    lib.pimd_guess_save.argtypes = [_P, ctypes.c_char_p]
+    lib.pimd_guess_load.argtypes = [_P, ctypes.c_char_p]
+    lib.pimd_ctx_set_guess_model.argtypes = [_P, _P]
+    lib.pimd_guess_pair_data.argtypes = [_P, ctypes.c_int, _I, _D, _D, _F, ctypes.c_int, ctypes.c_longlong, _I, _I,
+                                         _LL, _F, _D, _F, _D]
+    lib.pimd_guess_mlp_grad.argtypes = [_P, ctypes.c_int, ctypes.c_int, _F, _F, _D, _F, _F]
     lib.pimd_strerror.argtypes = [ctypes.c_int]
     lib.pimd_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -288,3 +309,121 @@ def pimd_peak_bench(device: int = 0) -> dict:
     _check(load().pimd_peak_bench(int(device), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "pimd_peak_bench")
     return {"fp64_tflops": a.value, "fp32_tflops": b.value, "dmma_fp64_tflops": c.value}
+
+
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+def _fp(a):
+    return a.ctypes.data_as(_FP) if a is not None else None
+
+
+class GuessModel:
+    """pimd_guess: the learned initial density (model, training set and
+    training on the device of the current CUDA device)."""
+
+    NTYPE = 9
+    NF = 96
+
+    def __init__(self, basis: Basis, seed: int = 0):
+        self.handle = _P()
+        _check(load().pimd_guess_create(ctypes.byref(self.handle), basis.handle, int(seed)), "pimd_guess_create")
+
+    @property
+    def nparam(self) -> int:
+        return int(load().pimd_guess_nparam(self.handle))
+
+    @property
+    def ndata(self) -> int:
+        return int(load().pimd_guess_ndata(self.handle))
+
+    def add_data(self, ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | None = None):
+        """Converge the SCF of the replicas coords[nrep, natom, 3] and add their
+        densities to the training set; returns the per-replica info."""
+        Z = np.ascontiguousarray(Z, np.int32)
+        X = np.ascontiguousarray(coords, np.float64)
+        opts = opts or scf_opts()
+        info = (PimdInfo * X.shape[0])()
+        _check(load().pimd_guess_add_data(self.handle, ctx.handle, X.shape[0], X.shape[1], _ip(Z), _dp(X),
+                                          basis.handle, ctypes.byref(opts), ctypes.cast(info, _P)),
+               "pimd_guess_add_data")
+        return _infos(info)
+
+    def clear_data(self):
+        load().pimd_guess_clear_data(self.handle)
+
+    def train(self, epochs: int, lr: float = 1e-3) -> np.ndarray:
+        hist = np.zeros(max(int(epochs), 1))
+        _check(load().pimd_guess_train(self.handle, int(epochs), float(lr), _dp(hist)), "pimd_guess_train")
+        return hist[:int(epochs)]
+
+    def loss(self) -> float:
+        v = np.zeros(1)
+        _check(load().pimd_guess_loss(self.handle, _dp(v)), "pimd_guess_loss")
+        return float(v[0])
+
+    def save(self, path: str):
+        _check(load().pimd_guess_save(self.handle, str(path).encode()), "pimd_guess_save")
+
+    def load_weights(self, path: str):
+        _check(load().pimd_guess_load(self.handle, str(path).encode()), "pimd_guess_load")
+
+    def attach(self, ctx: Context):
+        """Use this model for guess = 2 and 3 in ctx (the model must outlive
+        its use there)."""
+        _check(load().pimd_ctx_set_guess_model(ctx.handle, self.handle), "pimd_ctx_set_guess_model")
+
+    def pair_data(self, Z, coords, D=None, local_in=None, nbf=None):
+        """Test hook: pair rows of one molecule. Returns dict with pairs [n,2],
+        block_off [n], feats [n,96], frames [n,3,3], local (if D) and D_lab
+        (if local_in)."""
+        Z = np.ascontiguousarray(Z, np.int32)
+        X = np.ascontiguousarray(coords, np.float64)
+        n_at = len(Z)
+        npmax = n_at * (n_at + 1) // 2
+        noutmax = npmax * 14 * 14
+        npair = ctypes.c_int()
+        AB = np.zeros((npmax, 2), np.int32)
+        off = np.zeros(npmax, np.int64)
+        feats = np.zeros((npmax, self.NF), np.float32)
+        frames = np.zeros((npmax, 9))
+        Dh = np.ascontiguousarray(D, np.float64) if D is not None else None
+        loc_out = np.zeros(noutmax, np.float32) if D is not None else None
+        loc_in = None
+        Dout = None
+        if local_in is not None:
+            loc_in = np.zeros(noutmax, np.float32)
+            loc_in[:len(local_in)] = local_in
+            N = int(nbf) if nbf is not None else int(Dh.shape[0])
+            Dout = np.zeros((N, N))
+        rc = load().pimd_guess_pair_data(self.handle, n_at, _ip(Z), _dp(X), _dp(Dh) if Dh is not None else None,
+                                         _fp(loc_in), npmax, noutmax, ctypes.byref(npair), _ip(AB),
+                                         off.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _fp(feats),
+                                         _dp(frames), _fp(loc_out), _dp(Dout) if Dout is not None else None)
+        _check(rc, "pimd_guess_pair_data")
+        n = npair.value
+        out = dict(pairs=AB[:n].copy(), block_off=off[:n].copy(), feats=feats[:n].copy(),
+                   frames=frames[:n].reshape(n, 3, 3).copy())
+        if loc_out is not None:
+            out["local"] = loc_out
+        if Dout is not None:
+            out["D_lab"] = Dout
+        return out
+
+    def mlp_grad(self, type_: int, X, Y):
+        """Test hook: (loss, params, grads) of the network on X[n, 96], Y[n, width]."""
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        loss = np.zeros(1)
+        P = np.zeros(self.nparam, np.float32)
+        G = np.zeros(self.nparam, np.float32)
+        _check(load().pimd_guess_mlp_grad(self.handle, X.shape[0], int(type_), _fp(X), _fp(Y), _dp(loss), _fp(P),
+                                          _fp(G)), "pimd_guess_mlp_grad")
+        return float(loss[0]), P, G
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().pimd_guess_destroy(self.handle)
+        except Exception:
+            pass
