@@ -63,7 +63,11 @@ typedef struct {
     int guess;            /* 0 core Hamiltonian, 1 previous MOs of the same replica index (Sec. 2:
                              MOs of each replica reused as the next step's guess), falls back to 0;
                              2 learned density (the model attached by pimd_ctx_set_guess_model);
-                             3 previous MOs where cached, else the learned density */
+                             3 previous MOs where cached, else the learned density;
+                             4 superposition of spherically averaged atomic densities (SAD:
+                               fractional-occupation SCF of each isolated neutral atom, 1s 2s 2p
+                               configurations, Z <= 10, computed once per basis and element);
+                             5 previous MOs where cached, else SAD */
     int deterministic;    /* reserved, 0 */
     int want_gradient;    /* 1 */
 } pimd_scf_opts;
@@ -164,6 +168,9 @@ int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double
 int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coords, const pimd_basis* basis,
                       double* S, double* T, double* V);
 int pimd_boys_dev(pimd_ctx* ctx, int n, int m, const double* T_dev, double* F_dev);
+/* pimd_sad_atomic_density: the atomic density of element Z used by the SAD
+ * guess (guess = 4, 5), host array D[n][n], n = functions of Z in the basis. */
+int pimd_sad_atomic_density(pimd_ctx* ctx, const pimd_basis* basis, int Z, double* D, int n);
 
 /* Batched symmetric eigensolver of the SCF diagonalisation step (the
  * Roothaan-Hall eigenproblem solved in every SCF cycle, Sec. 3.1): nmat

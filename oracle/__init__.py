@@ -15,4 +15,5 @@ standard analytic RHF gradient (see `rhf.py`).
 from .rhf import (OracleBasis, boys, build, core_guess, eri_block, eri_full,  # noqa: F401
                   jk, nuclear_repulsion, one_electron, rhf_energy_gradient,
                   run_scf, schwarz, num_threads, grad_1e, grad_2e, normalise_shell,
-                  eri_list, deriv_list, canonical_quartets, g_block)
+                  eri_list, deriv_list, canonical_quartets, g_block,
+                  sad_atomic_density, orthogonaliser)

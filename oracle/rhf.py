@@ -362,6 +362,55 @@ def run_scf(ob: OracleBasis, Z, xyz, conv_energy=1e-10, conv_error=1e-8, max_ite
     return SCFResult(E, Dg, W, C, eps, it, converged, S, h, F, e_nn, nq, gap)
 
 
+def sad_atomic_density(basis: dict, Z: int, tol: float = 1e-9, max_iter: int = 200) -> np.ndarray:
+    """Spherically averaged density of the isolated neutral atom Z (<= 10) in
+    `basis`, the building block of the superposition-of-atomic-densities
+    guess (the paper has no such guess; it reuses the previous step's MOs).
+
+    Configuration 1s^2 2s^2 2p^(Z-4): the first two s orbitals (lowest orbital
+    energies among the s-type eigenvectors) take min(electrons left, 2) each,
+    the electrons left after them are shared evenly by the three lowest p-type
+    eigenvectors. Orbitals are told apart by angular momentum, not energy
+    order (in a fractional-occupation SCF the 2s can lie above the 2p).
+    Iterate F = h + J(D) - K(D)/2 -> eigenvectors -> D = sum_k n_k C_k C_k^T,
+    starting from the eigenvectors of h, until max|D_new - D| < tol.
+    """
+    Zs = np.array([Z], np.int32)
+    xyz = np.zeros((1, 3))
+    ob = OracleBasis.build(basis, Zs, xyz)
+    S, T, V = one_electron(ob, Zs, xyz)
+    h = T + V
+    X = orthogonaliser(S)
+    lfun = np.concatenate([[sh.l] * (2 * sh.l + 1) for sh in basis[int(Z)]])
+
+    def occupied_density(F):
+        eps, Cp = np.linalg.eigh(X.T @ F @ X)
+        C = X @ Cp
+        lk = [int(np.argmax([np.sum(C[lfun == l, k] ** 2) for l in range(3)])) for k in range(C.shape[1])]
+        n = np.zeros(C.shape[1])
+        left = int(Z)
+        s_orb = [k for k in np.argsort(eps, kind="stable") if lk[k] == 0][:2]
+        p_orb = [k for k in np.argsort(eps, kind="stable") if lk[k] == 1][:3]
+        for k in s_orb:
+            n[k] = min(left, 2)
+            left -= int(n[k])
+        if left > 0:
+            if len(p_orb) < 3 or left > 6:
+                raise ValueError("configuration needs a 2p shell")
+            n[p_orb] = left / 3.0
+        return (C * n) @ C.T
+
+    D = occupied_density(h)
+    for _ in range(max_iter):
+        J, K, _ = jk(ob, D)
+        Dn = occupied_density(h + J - 0.5 * K)
+        diff = float(np.abs(Dn - D).max())
+        D = Dn
+        if diff < tol:
+            break
+    return D
+
+
 def rhf_energy_gradient(basis: dict, Z, xyz, want_gradient=True, tau=1e-12, **kw):
     """Converged RHF energy (Eh) and gradient dE/dR (Eh/bohr, [natom, 3])."""
     ob = OracleBasis.build(basis, Z, xyz)

@@ -125,6 +125,10 @@ void launch_shell_bounds(const Shells& S, const Reps& R, int nrep, int maxsh, co
 void launch_delta_density(const RepMat* rm, int nrep, const double* D, double* Dprev, double* dD, double* G,
                           const int* mode, cudaStream_t st);
 
+// D[rep] block (f0..f0+n)^2 <- src[off..off+n*n] for each descriptor {rep, f0, n, off}
+void launch_place_blocks(const RepMat* rm, const int* desc4, int nblk, const double* src, double* D,
+                         cudaStream_t st);
+
 // ------------------------------------------------------------------ learned guess
 // shells (angular momenta into l_out, at most maxsh) of element Z: count, or -1
 int basis_elem_shells(const pimd_basis* b, int Z, int* l_out, int maxsh);

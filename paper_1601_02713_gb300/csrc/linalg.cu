@@ -614,6 +614,23 @@ void launch_copy_mats(const RepMat* rm, int nrep, const double* src, double* dst
     copy_mats_kernel<<<elem_grid(nrep), 256, 0, st>>>(rm, src, dst, mask);
 }
 
+// one block per descriptor {rep, f0, n, off}: an n x n diagonal block of D[rep]
+__global__ void place_blocks_kernel(const RepMat* rms, const int* desc, int nblk, const double* src, double* D)
+{
+    const int b = blockIdx.x;
+    if (b >= nblk) return;
+    const int rep = desc[4 * b], f0 = desc[4 * b + 1], n = desc[4 * b + 2], off = desc[4 * b + 3];
+    const RepMat rm = rms[rep];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+        D[rm.off + (size_t)(f0 + e / n) * rm.N + f0 + e % n] = src[(size_t)off + e];
+}
+
+void launch_place_blocks(const RepMat* rm, const int* desc4, int nblk, const double* src, double* D,
+                         cudaStream_t st)
+{
+    if (nblk > 0) place_blocks_kernel<<<nblk, 128, 0, st>>>(rm, desc4, nblk, src, D);
+}
+
 void diis_set_stride(long long stride) { g_diis_stride = stride; }
 
 void launch_diis_store(const RepMat* rm, int nrep, const double* F, const double* E, double* Fh, double* Eh,

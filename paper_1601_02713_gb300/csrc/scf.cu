@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -44,7 +45,10 @@ struct pimd_basis {
     // flattened primitives (element-major, shell order) for the device
     std::vector<double> exps, coefs;
     std::vector<std::vector<int>> prim_off;  // per element, per shell
+    long long uid = 0;                       // distinct per basis created in the process
 };
+
+static std::atomic<long long> g_basis_uid{1};
 
 static double dfact(int n)
 {
@@ -99,6 +103,8 @@ struct pimd_ctx {
     cudaEvent_t ev[8];
     int nsm = 152;
     pimd_guess* guess_model = nullptr;   // not owned (guess = 2, 3)
+    // SAD guess: atomic densities per (basis uid, Z), row-major nbf x nbf
+    std::map<std::pair<long long, int>, std::vector<double>> sad;
 };
 
 static int set_err(pimd_ctx* ctx, int code, const std::string& msg)
@@ -251,6 +257,7 @@ extern "C" int pimd_basis_create(pimd_basis** out, int nelem, const int* Z_of_el
         return PIMD_EINVAL;
     if (spherical != 1) return PIMD_EINVAL;
     pimd_basis* b = new pimd_basis();
+    b->uid = g_basis_uid++;
     int s = 0, p = 0;
     for (int e = 0; e < nelem; e++) {
         const int Z = Z_of_elem[e];
@@ -335,6 +342,7 @@ extern "C" int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out)
 // ---------------------------------------------------------------------------
 struct Batch {
     int nrep = 0;
+    bool allow_odd = false;     // isolated atoms of the SAD guess (occupations set by the caller)
     std::vector<int> natom, atom0, nbf, nocc;
     std::vector<int> atom_f0;   // first function of each atom within its replica
     int* d_Zi = nullptr;        // nuclear charges (int) on the device
@@ -421,7 +429,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
             Zd.push_back((double)Z);
             atom_rep.push_back(r);
         }
-        if (nel % 2) return set_err(ctx, PIMD_EINVAL, "odd electron count (RHF needs a closed shell)");
+        if (nel % 2 && !bt.allow_odd) return set_err(ctx, PIMD_EINVAL, "odd electron count (RHF needs a closed shell)");
         if (nbf > 768) return set_err(ctx, PIMD_EINVAL, "more than 768 basis functions in one replica");
         bt.nbf[r] = nbf;
         bt.nocc[r] = nel / 2;
@@ -789,13 +797,171 @@ static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32
     return PIMD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// SAD guess: superposition of spherically averaged atomic densities
+// ---------------------------------------------------------------------------
+// Each element's density comes from an SCF of the isolated neutral atom in
+// the same basis, with the configuration 1s^2 2s^2 2p^n (Z <= 10) and the
+// partly filled p shell spread evenly over its three orbitals, so that the
+// density stays spherical. Orbitals are occupied by angular momentum (the
+// lowest s orbitals, then the lowest p triplet), not by energy order: in a
+// fractional-occupation atomic SCF the 2s can rise above the 2p. The atom's
+// Fock matrix has no s-p-d mixing, so every eigenvector has one l.
+// Integrals, Fock builds, diagonalisations and densities run in the kernels
+// of the molecular SCF; the host picks the occupied orbitals from the
+// eigenvectors' l and stops when no density element changes by 1e-9 or more.
+static int sad_atomic(pimd_ctx* ctx, const pimd_basis* basis, const std::vector<int>& Zs)
+{
+    const int n = (int)Zs.size();
+    std::vector<int> natom(n, 1);
+    std::vector<double> xyz(3 * (size_t)n, 0.0);
+    double* d_xyz;
+    UPLOAD("sad_xyz", xyz, d_xyz);
+    Batch bt;
+    bt.allow_odd = true;
+    int rc = setup_batch(ctx, bt, n, natom.data(), Zs.data(), d_xyz, basis, 1e-12);
+    if (rc) return rc;
+    // per replica (atom): angular momentum of every function
+    std::vector<std::vector<int>> lfun(n);
+    for (int r = 0; r < n; r++) {
+        for (int sh = bt.rep_sh0[r]; sh < bt.rep_sh0[r + 1]; sh++)
+            for (int k = 0; k < nsph(bt.sh_l[sh]); k++) lfun[r].push_back(bt.sh_l[sh]);
+        bt.nocc[r] = bt.nbf[r];   // densities over all columns, unoccupied ones weighted 0
+    }
+    Mats m;
+    if ((rc = alloc_mats(ctx, bt, m, 2))) return rc;
+    ScfPlan plan;
+    if ((rc = make_plan(ctx, bt, m, plan))) return rc;
+    std::vector<int> active(n, 1), mode(n, 2);
+    UPLOAD("active", active, m.active);
+    bt.R.active = m.active;
+    int* d_mode;
+    UPLOAD("sad_mode", mode, d_mode);
+    cudaStream_t st = ctx->stream;
+    launch_one_electron(bt.P, bt.S, bt.B, bt.At, bt.R, m.S, m.T, m.V, ctx->boys, st);
+    add_mats(m.rm, n, m.T, m.V, m.H, st);
+    CK(cudaMemsetAsync(m.enn, 0, sizeof(double) * n, st));
+    launch_jacobi(m.rm, n, m.S, m.Cp, m.Ev, m.ldE, m.work, nullptr, 0, st);
+    launch_orth_from_eig(m.rm, n, m.Cp, m.Ev, m.ldE, m.X, st);
+    launch_copy_mats(m.rm, n, m.H, m.Fb, nullptr, st);
+    std::vector<double> C(bt.mtot), ev((size_t)n * m.ldE), half((size_t)n * m.ldE);
+    // Fb -> orbitals -> D = sum_k occ_k C_k C_k^T (W = 2 Cs C^T with Cs = C occ/2)
+    auto density = [&]() -> int {
+        launch_identity(m.rm, n, m.Cq, nullptr, st);
+        diag_density(ctx, bt, m, plan, nullptr);
+        CK(cudaMemcpyAsync(C.data(), m.C, sizeof(double) * bt.mtot, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ev.data(), m.Ev, sizeof(double) * ev.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::fill(half.begin(), half.end(), 0.0);
+        for (int r = 0; r < n; r++) {
+            const int N = bt.nbf[r];
+            const double* Cr = C.data() + bt.moff[r];
+            std::vector<int> ls(N);
+            for (int k = 0; k < N; k++) {
+                double w[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < N; i++) w[lfun[r][i]] += Cr[(size_t)i * N + k] * Cr[(size_t)i * N + k];
+                ls[k] = (int)(std::max_element(w, w + 3) - w);
+            }
+            int left = Zs[r], ns = 0, np = 0;
+            std::vector<int> pk;
+            for (int k = 0; k < N; k++) {   // eigenvalues ascending
+                if (ls[k] == 0 && ns < 2 && left > 0) {
+                    const int x = std::min(left, 2);
+                    half[(size_t)r * m.ldE + k] = 0.5 * x;
+                    left -= x;
+                    ns++;
+                } else if (ls[k] == 1 && np < 3) {
+                    pk.push_back(k);
+                    np++;
+                }
+            }
+            if (left > 0) {
+                if ((int)pk.size() < 3 || left > 6) return PIMD_EINVAL;
+                for (int k : pk) half[(size_t)r * m.ldE + k] = 0.5 * left / 3.0;
+            }
+        }
+        double* d_half;
+        UPLOAD("sad_half", half, d_half);
+        launch_scale_cols(m.rm, n, m.C, d_half, m.ldE, m.Cs, nullptr, st);
+        gemm(ctx, plan.Wn, nullptr);
+        launch_copy_mats(m.rm, n, m.W, m.D, nullptr, st);
+        return PIMD_OK;
+    };
+    std::vector<double> D(bt.mtot), Dn(bt.mtot);
+    auto fetch = [&](std::vector<double>& out) -> int {
+        CK(cudaMemcpyAsync(out.data(), m.D, sizeof(double) * bt.mtot, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return PIMD_OK;
+    };
+    if ((rc = density())) return set_err(ctx, rc, "SAD: atom without a 2p shell in the basis");
+    if ((rc = fetch(D))) return rc;
+    bool conv = false;
+    for (int it = 1; it <= 200 && !conv; it++) {
+        launch_delta_density(m.rm, n, m.D, m.Dp, m.dD, m.G, d_mode, st);
+        if ((rc = fock_build(ctx, bt, m, 1e-12, 0.0, m.dD))) return rc;
+        launch_fock_assemble(m.rm, n, m.H, m.G, m.F, m.active, st);
+        launch_copy_mats(m.rm, n, m.F, m.Fb, nullptr, st);
+        if ((rc = density())) return set_err(ctx, rc, "SAD: atom without a 2p shell in the basis");
+        if ((rc = fetch(Dn))) return rc;
+        double diff = 0.0;
+        for (long long e = 0; e < bt.mtot; e++) {
+            if (!std::isfinite(Dn[e])) return set_err(ctx, PIMD_ECUDA, "SAD: non-finite atomic density");
+            diff = std::max(diff, fabs(Dn[e] - D[e]));
+        }
+        D.swap(Dn);
+        conv = diff < 1e-9;
+    }
+    // an atomic SCF still short of the 1e-9 bound after 200 cycles keeps its last
+    // density: the molecular SCF converges from any starting density
+    CK(cudaGetLastError());
+    for (int r = 0; r < n; r++)
+        ctx->sad[{basis->uid, Zs[r]}] =
+            std::vector<double>(D.begin() + bt.moff[r], D.begin() + bt.moff[r] + (size_t)bt.nbf[r] * bt.nbf[r]);
+    return PIMD_OK;
+}
+
+// atomic densities of every element in Zc[0..natot) present in the cache
+static int sad_ensure(pimd_ctx* ctx, const pimd_basis* basis, const int* Zc, int natot)
+{
+    std::vector<int> need;
+    for (int a = 0; a < natot; a++) {
+        const int Z = Zc[a];
+        if (Z < 1 || Z > 10) return set_err(ctx, PIMD_EINVAL, "SAD guess: elements up to Z = 10 only");
+        if (!basis->elem.count(Z)) return set_err(ctx, PIMD_EINVAL, "element missing from basis");
+        if (!ctx->sad.count({basis->uid, Z}) && std::find(need.begin(), need.end(), Z) == need.end())
+            need.push_back(Z);
+    }
+    if (need.empty()) return PIMD_OK;
+    return sad_atomic(ctx, basis, need);
+}
+
+extern "C" int pimd_sad_atomic_density(pimd_ctx* ctx, const pimd_basis* basis, int Z, double* D, int n)
+{
+    if (!ctx || !basis || !D) return PIMD_EINVAL;
+    auto it = basis->elem.find(Z);
+    if (it == basis->elem.end() || basis->nbf_elem[it->second] != n) return PIMD_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    int rc = sad_ensure(ctx, basis, &Z, 1);
+    if (rc) return rc;
+    const auto& Da = ctx->sad.at({basis->uid, Z});
+    std::copy(Da.begin(), Da.end(), D);
+    return PIMD_OK;
+}
+
 static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc, const double* d_xyz,
                      const pimd_basis* basis, const pimd_scf_opts* o, double* d_E, double* d_grad, pimd_info* info)
 {
     Batch bt;
     ctx->stats = pimd_stats{};
     CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-    int rc = setup_batch(ctx, bt, nrep, natom_of, Zc, d_xyz, basis, o->schwarz_tau);
+    const bool want_sad = o->guess == 4 || o->guess == 5;
+    int rc = PIMD_OK;
+    if (want_sad) {
+        int natot = 0;
+        for (int r = 0; r < nrep; r++) natot += natom_of[r];
+        if ((rc = sad_ensure(ctx, basis, Zc, natot))) return rc;
+    }
+    rc = setup_batch(ctx, bt, nrep, natom_of, Zc, d_xyz, basis, o->schwarz_tau);
     if (rc) return rc;
     const int hist = std::max(2, std::min(8, o->diis_size));
     Mats m;
@@ -833,19 +999,21 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     launch_orth_from_eig(m.rm, nrep, m.Cp, m.Ev, m.ldE, m.X, ctx->stream);
     // guess per replica: cached MOs of the same replica index (guess 1, 3),
     // else the learned density (guess 2, 3), else the core Hamiltonian
-    const bool want_cache = o->guess == 1 || o->guess == 3;
+    const bool want_cache = o->guess == 1 || o->guess == 3 || o->guess == 5;
     const bool want_learned = o->guess == 2 || o->guess == 3;
     if (want_learned && !ctx->guess_model) return set_err(ctx, PIMD_EINVAL, "learned guess without a model");
     if ((int)ctx->mo.size() < nrep) ctx->mo.resize(nrep);
-    std::vector<int> use_cache(nrep, 0), core(nrep, 0), learned(nrep, 0);
-    int nlearned = 0;
+    std::vector<int> use_cache(nrep, 0), core(nrep, 0), learned(nrep, 0), sadm(nrep, 0);
+    int nlearned = 0, nsad = 0;
     for (int r = 0; r < nrep; r++) {
         auto& mo = ctx->mo[r];
         std::vector<int> z(Zc + bt.atom0[r], Zc + bt.atom0[r + 1]);
         use_cache[r] = (want_cache && mo.N == bt.nbf[r] && mo.Z == z);
         learned[r] = !use_cache[r] && want_learned;
-        core[r] = !use_cache[r] && !learned[r];
+        sadm[r] = !use_cache[r] && want_sad;
+        core[r] = !use_cache[r] && !learned[r] && !sadm[r];
         nlearned += learned[r];
+        nsad += sadm[r];
         if (use_cache[r])
             CK(cudaMemcpyAsync(m.C + bt.moff[r], mo.C.p, sizeof(double) * bt.nbf[r] * bt.nbf[r],
                                cudaMemcpyDeviceToDevice, ctx->stream));
@@ -877,6 +1045,33 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
                                   m.rm, d_ml, m.S, m.dD, bt.mtot, m.D, ctx->stream);
         if (rc) return set_err(ctx, rc, "learned guess failed");
         ctx->stats.kernel_launches += 19;
+    }
+    if (nsad > 0) {
+        // block-diagonal D of the atomic densities (tr(D S) = electrons exactly)
+        std::vector<double> tab;
+        std::map<int, int> toff;
+        std::vector<int> desc;
+        for (int r = 0; r < nrep; r++) {
+            if (!sadm[r]) continue;
+            for (int a = bt.atom0[r]; a < bt.atom0[r + 1]; a++) {
+                const auto& Da = ctx->sad.at({basis->uid, Zc[a]});
+                if (!toff.count(Zc[a])) {
+                    toff[Zc[a]] = (int)tab.size();
+                    tab.insert(tab.end(), Da.begin(), Da.end());
+                }
+                const int na = (int)lround(sqrt((double)Da.size()));
+                desc.insert(desc.end(), {r, bt.atom_f0[a], na, toff[Zc[a]]});
+            }
+        }
+        double* d_tab;
+        int *d_desc, *d_ms;
+        UPLOAD("sad_tab", tab, d_tab);
+        UPLOAD("sad_desc", desc, d_desc);
+        UPLOAD("mask_sad", sadm, d_ms);
+        CK(cudaMemsetAsync(m.dD, 0, sizeof(double) * bt.mtot, ctx->stream));
+        launch_place_blocks(m.rm, d_desc, (int)desc.size() / 4, d_tab, m.dD, ctx->stream);
+        launch_copy_mats(m.rm, nrep, m.dD, m.D, d_ms, ctx->stream);
+        ctx->stats.kernel_launches += 2;
     }
     // SCF iterations
     std::vector<double> E(nrep), emax(nrep), Eprev(nrep, 0.0);
@@ -1072,7 +1267,7 @@ static int check_common(pimd_ctx* ctx, const pimd_basis* basis, const pimd_scf_o
         memcpy(&o, opts, opts->struct_size);
     }
     if (!(o.conv_energy > 0) || !(o.conv_error > 0) || o.max_iter < 1 || o.max_iter > 10000 ||
-        !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 3)
+        !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 5)
         return set_err(ctx, PIMD_EINVAL, "bad SCF options");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
     return PIMD_OK;

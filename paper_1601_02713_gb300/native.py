@@ -105,6 +105,7 @@ def load(path: str | None = None):
     lib.pimd_guess_pair_data.argtypes = [_P, ctypes.c_int, _I, _D, _D, _F, ctypes.c_int, ctypes.c_longlong, _I, _I,
                                          _LL, _F, _D, _F, _D]
     lib.pimd_guess_mlp_grad.argtypes = [_P, ctypes.c_int, ctypes.c_int, _F, _F, _D, _F, _F]
+    lib.pimd_sad_atomic_density.argtypes = [_P, _P, ctypes.c_int, _D, ctypes.c_int]
     lib.pimd_strerror.argtypes = [ctypes.c_int]
     lib.pimd_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -280,6 +281,14 @@ def pimd_one_electron(ctx: Context, basis: Basis, Z, coords):
 def pimd_boys_dev(ctx: Context, T_dev, m: int, F_dev):
     _check(load().pimd_boys_dev(ctx.handle, int(T_dev.numel()), int(m), _P(T_dev.data_ptr()),
                                 _P(F_dev.data_ptr())), "pimd_boys_dev")
+
+
+def pimd_sad_atomic_density(ctx: Context, basis: Basis, Z: int):
+    """Atomic density of element Z used by the SAD guess ([n, n] host array)."""
+    n = basis.nbf([Z])
+    D = np.zeros((n, n))
+    _check(load().pimd_sad_atomic_density(ctx.handle, basis.handle, int(Z), _dp(D), n), "pimd_sad_atomic_density")
+    return D
 
 
 def pimd_last_stats(ctx: Context) -> dict:

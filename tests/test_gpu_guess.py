@@ -282,3 +282,44 @@ def test_learned_guess_errors(ctx, spd):
         native.pimd_bo_forces(c2, B, Z, X[None], native.scf_opts(guess=2))
     assert e.value.code == native.PIMD_EINVAL
     c2.close()
+
+
+# ------------------------------------------------------------------ SAD guess
+@pytest.mark.parametrize("kind,Z", [("split_spd", 8), ("split_spd", 6), ("split_spd", 1), ("min_sp", 8),
+                                    ("min_sp", 1)])
+def test_sad_atomic_density_against_oracle(ctx, kind, Z):
+    bas = inputs.basis_set(kind)
+    B = native.Basis(bas)
+    D = native.pimd_sad_atomic_density(ctx, B, Z)
+    np.testing.assert_allclose(D, O.sad_atomic_density(bas, Z), atol=1e-7)
+
+
+def test_sad_guess_same_answer(ctx, spd):
+    bas, B = spd
+    r, _ = inputs.workload("water8_spd_32beads", nrep=2)
+    Z, X = r.stacked()
+    ctx.clear_guess()
+    E0, G0, i0, _ = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=0))
+    E1, G1, i1, _ = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=4))
+    assert all(i["converged"] for i in i0 + i1)
+    np.testing.assert_allclose(E1, E0, atol=E_TOL, rtol=0)
+    np.testing.assert_allclose(G1, G0, atol=G_TOL, rtol=0)
+    # guess = 5: the second call starts from the cached MOs
+    ctx.clear_guess()
+    native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=5))
+    E2, _, i2, _ = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=5))
+    np.testing.assert_allclose(E2, E0, atol=E_TOL, rtol=0)
+    assert max(i["iterations"] for i in i2) <= 3
+
+
+def test_sad_guess_ragged_images(ctx, spd):
+    """C, H and O atoms; images of different sizes in one call."""
+    bas, B = spd
+    reps, _ = inputs.workload("da_images_24")
+    sub = inputs.Replicas([reps.Z[i] for i in (0, 7)], [reps.coords[i] for i in (0, 7)])
+    nat, Zc, Xc = sub.concat()
+    E0, G0, i0, _ = native.string_images_forces(ctx, B, nat, Zc, Xc, native.scf_opts(guess=0))
+    E1, G1, i1, _ = native.string_images_forces(ctx, B, nat, Zc, Xc, native.scf_opts(guess=4))
+    assert all(i["converged"] for i in i0 + i1)
+    np.testing.assert_allclose(E1, E0, atol=E_TOL, rtol=0)
+    np.testing.assert_allclose(G1, G0, atol=G_TOL, rtol=0)
