@@ -56,6 +56,12 @@ def parse():
     ap.add_argument("--cpu-sample-deriv", type=int, default=8000)
     ap.add_argument("--fp32-tau", type=float, default=0.0,
                     help="mixed precision: quartets with Q_ab Q_cd max|dD| below this run in FP32 (0: all FP64)")
+    ap.add_argument("--guess-study", action="store_true",
+                    help="instead of the benchmark line: train the learned density guess on the GPU and compare "
+                         "SCF iterations and evals/s of the guesses (one JSON line)")
+    ap.add_argument("--train-clusters", type=int, default=8)
+    ap.add_argument("--train-beads", type=int, default=16)
+    ap.add_argument("--train-epochs", type=int, default=400)
     return ap.parse_args()
 
 
@@ -191,11 +197,95 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- learned-guess study
+def run_guess_study(args):
+    """Train the learned density guess on converged (H2O)8 bead densities
+    (seeded clusters other than the benchmark's, mixed-precision SCF), then run
+    the benchmark's beads (energy + gradient) from each starting guess and in
+    each form: plain per-bead FP64 calls (SAD guess), batched FP64 (core,
+    SAD, learned, previous-step MOs) and batched mixed precision (learned,
+    previous-step MOs). Reports SCF iterations, bead evals/s and the largest
+    energy and gradient deviation from the batched FP64 SAD run."""
+    import torch
+    from paper_1601_02713_gb300 import build as B
+    B.build()
+    from paper_1601_02713_gb300 import native
+    torch.cuda.set_device(0)
+    seq, kind = make_steps(args.workload, args.nrep, 2, 0)
+    Z, X0 = seq[0].stacked()
+    _, X1 = seq[1].stacked()
+    nrep = len(X0)
+    basis = native.Basis(inputs.basis_set(kind))
+    ctx = native.Context(0)
+    model = native.GuessModel(basis, seed=5)
+    t0 = time.perf_counter()
+    ntrain = 0
+    for reps in inputs.water_cluster_set(len(Z) // 3, args.train_clusters, args.train_beads, 500):
+        Zt, Xt = reps.stacked()
+        model.add_data(ctx, basis, Zt, Xt, native.scf_opts(guess=4, fp32_tau=1e-6, want_gradient=0))
+        ntrain += len(Xt)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = model.train(args.train_epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    model.attach(ctx)
+
+    def run(X, guess, fp32_tau, per_bead=False):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        if per_bead:
+            out = [native.pimd_bo_forces(ctx, basis, Z, X[i:i + 1], native.scf_opts(guess=guess, fp32_tau=fp32_tau))
+                   for i in range(len(X))]
+            E = np.concatenate([o[0] for o in out])
+            G = np.concatenate([o[1] for o in out])
+            info = [o[2][0] for o in out]
+        else:
+            E, G, info, _ = native.pimd_bo_forces(ctx, basis, Z, X, native.scf_opts(guess=guess, fp32_tau=fp32_tau))
+        dt = time.perf_counter() - t
+        assert all(i["converged"] for i in info)
+        return E, G, float(np.mean([i["iterations"] for i in info])), len(X) / dt
+
+    rows = []
+    ctx.clear_guess()
+    Eref, Gref, it, v = run(X0, 4, 0.0)
+    rows.append(("batched", "fp64", "SAD", it, v, Eref, Gref))
+    for form, prec, guess, tau, per in [("per-bead", "fp64", "SAD", 0.0, True), ("batched", "fp64", "core", 0.0, False),
+                                        ("batched", "fp64", "learned", 0.0, False),
+                                        ("batched", "mixed", "learned", 1e-6, False)]:
+        ctx.clear_guess()
+        g = {"SAD": 4, "core": 0, "learned": 2}[guess]
+        E, G, it, v = run(X0, g, tau, per)
+        rows.append((form, prec, guess, it, v, E, G))
+    # previous-step MOs: converge the step before, then time the step
+    for prec, tau in [("fp64", 0.0), ("mixed", 1e-6)]:
+        ctx.clear_guess()
+        run(X0, 4, tau)
+        E1, G1, it, v = run(X1, 1, tau)
+        rows.append(("batched", prec, "previous-step MOs (next MD step)", it, v, None, None))
+    out = {"study": "learned SCF guess", "workload": args.workload, "beads": nrep, "basis": kind,
+           "training": {"geometries": ntrain, "system": f"(H2O){len(Z) // 3} seeded clusters 500..",
+                        "data_s": t_data, "epochs": args.train_epochs, "train_s": t_train,
+                        "loss_first": float(hist[0]), "loss_last": float(hist[-1])},
+           "rows": []}
+    for form, prec, guess, it, v, E, G in rows:
+        r = {"form": form, "precision": prec, "guess": guess, "scf_iterations_mean": it, "bead_evals_per_s": v}
+        if E is not None:
+            r["max_abs_dE_vs_fp64_sad"] = float(np.abs(E - Eref).max())
+            r["max_abs_dG_vs_fp64_sad"] = float(np.abs(G - Gref).max())
+        out["rows"].append(r)
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 # ---------------------------------------------------------------- ours
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.guess_study:
+        return run_guess_study(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -292,6 +382,9 @@ def main():
             "fp32_quartet_fraction": (sum(s["quartets_fp32"] for s in stats)
                                       / max(1, sum(s["quartets_fp32"] + s["quartets_fp64"] for s in stats))),
             "fock_builds_per_step": builds / K,
+            "ms_split_per_step": {"fock": fock_ms / K, "grad2e": sum(s["ms_grad2e"] for s in stats) / K,
+                                  "other": (t_local * 1000.0 - fock_ms - sum(s["ms_grad2e"] for s in stats)) / K},
+            "eri_flops32_per_step": sum(s["eri_flops32_per_build"] * s["fock_builds"] for s in stats) / K,
             "scf_iterations_mean": statistics.mean(iters),
             "roofline": {"kernel": "jk_kernel (one Fock build = all quartet classes)", "bound": "alu",
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -70,6 +70,10 @@ typedef struct {
                              5 previous MOs where cached, else SAD */
     int deterministic;    /* reserved, 0 */
     int want_gradient;    /* 1 */
+    int use_graphs;       /* 1: from the second SCF iteration on, each iteration's kernel sequence
+                             (density increment + Fock build; Fock assembly, energy and DIIS error;
+                             DIIS extrapolation + diagonalisation + density) is replayed as three
+                             CUDA graphs captured from the first; 0: plain launches */
 } pimd_scf_opts;
 
 /* Per-replica result record. */

@@ -243,25 +243,18 @@ __device__ void shell_rot(int l, const double* U, double* M)
     }
 }
 
-__device__ void atom_rot(const ElemShells& es, int e, const double* U, double* M)
+// element (i, j) of the representation of shell angular momentum l
+// (s: 1; p: Rp; d: Rd)
+__device__ __forceinline__ double rep_el(int l, const double* Rp, const double* Rd, int i, int j)
 {
-    const int n = es.nbf[e];
-    for (int i = 0; i < n * n; i++) M[i] = 0.0;
-    int o = 0;
-    for (int s = 0; s < es.nsh[e]; s++) {
-        const int l = es.l[e][s];
-        const int k = nsph(l);
-        double R[25];
-        shell_rot(l, U, R);
-        for (int i = 0; i < k; i++)
-            for (int j = 0; j < k; j++) M[(o + i) * n + o + j] = R[i * k + j];
-        o += k;
-    }
+    return l == 0 ? 1.0 : (l == 1 ? Rp[i * 3 + j] : Rd[i * 5 + j]);
 }
 
-// to_local = 1: blocks <- M_A^T D_AB M_B (float); else D_AB <- M_A L M_B^T
-// (and D_BA its transpose) for the pairs within the cutoff, L the block with
-// same-atom blocks symmetrised
+// The atoms' representations are block diagonal over their shells, so a
+// block is rotated shell pair by shell pair:
+// to_local = 1: blocks <- M_A^T D_AB M_B (float);
+// to_local = 0: D_AB <- M_A L M_B^T (and D_BA its transpose) for the pairs
+// within the cutoff, L the predicted block with same-atom blocks symmetrised.
 __global__ void block_rotate_kernel(const GuessPair* pairs, int npair, const double* frames, ElemShells es,
                                     const int* Zat, const RepMat* rms, double* Dmat, float* blocks,
                                     const int* within, int to_local)
@@ -271,45 +264,47 @@ __global__ void block_rotate_kernel(const GuessPair* pairs, int npair, const dou
     const GuessPair gp = pairs[q];
     if (!to_local && !within[q]) return;
     const int eA = elem_index(Zat[gp.A]), eB = elem_index(Zat[gp.B]);
-    const int na = es.nbf[eA], nb = es.nbf[eB];
-    double MA[G_MAXBF * G_MAXBF], MB[G_MAXBF * G_MAXBF], T[G_MAXBF * G_MAXBF];
-    atom_rot(es, eA, frames + 9 * (size_t)q, MA);
-    atom_rot(es, eB, frames + 9 * (size_t)q, MB);
+    if (eA < 0 || eB < 0) return;
+    const int nb = es.nbf[eB];
+    const double* U = frames + 9 * (size_t)q;
+    double Rp[9], Rd[25];
+    shell_rot(1, U, Rp);
+    shell_rot(2, U, Rd);
     const int N = rms[gp.rep].N;
     double* D = Dmat + rms[gp.rep].off;
     float* blk = blocks + gp.out_off;
-    if (to_local) {
-        for (int i = 0; i < na; i++)
-            for (int j = 0; j < nb; j++) {
-                double s = 0.0;
-                for (int k = 0; k < nb; k++) s += D[(size_t)(gp.fa + i) * N + gp.fb + k] * MB[k * nb + j];
-                T[i * nb + j] = s;
-            }
-        for (int i = 0; i < na; i++)
-            for (int j = 0; j < nb; j++) {
-                double s = 0.0;
-                for (int k = 0; k < na; k++) s += MA[k * na + i] * T[k * nb + j];
-                blk[i * nb + j] = (float)s;
-            }
-    } else {
-        const bool same = gp.A == gp.B;
-        for (int i = 0; i < na; i++)
-            for (int j = 0; j < nb; j++) {
-                double s = 0.0;
-                for (int k = 0; k < nb; k++) {
-                    const double L = same ? 0.5 * ((double)blk[i * nb + k] + (double)blk[k * nb + i])
-                                          : (double)blk[i * nb + k];
-                    s += L * MB[j * nb + k];
+    const bool same = gp.A == gp.B;
+    int oa = 0;
+    for (int sa = 0; sa < es.nsh[eA]; sa++) {
+        const int la = es.l[eA][sa], ka = nsph(la);
+        int ob = 0;
+        for (int sb = 0; sb < es.nsh[eB]; sb++) {
+            const int lb = es.l[eB][sb], kb = nsph(lb);
+            for (int i = 0; i < ka; i++)
+                for (int j = 0; j < kb; j++) {
+                    double s = 0.0;
+                    for (int k = 0; k < ka; k++)
+                        for (int l = 0; l < kb; l++) {
+                            if (to_local) {
+                                const double d = D[(size_t)(gp.fa + oa + k) * N + gp.fb + ob + l];
+                                s += rep_el(la, Rp, Rd, k, i) * d * rep_el(lb, Rp, Rd, l, j);
+                            } else {
+                                const int r = oa + k, c = ob + l;
+                                const double L = same ? 0.5 * ((double)blk[r * nb + c] + (double)blk[c * nb + r])
+                                                      : (double)blk[r * nb + c];
+                                s += rep_el(la, Rp, Rd, i, k) * L * rep_el(lb, Rp, Rd, j, l);
+                            }
+                        }
+                    if (to_local) {
+                        blk[(oa + i) * nb + ob + j] = (float)s;
+                    } else {
+                        D[(size_t)(gp.fa + oa + i) * N + gp.fb + ob + j] = s;
+                        if (!same) D[(size_t)(gp.fb + ob + j) * N + gp.fa + oa + i] = s;
+                    }
                 }
-                T[i * nb + j] = s;
-            }
-        for (int i = 0; i < na; i++)
-            for (int j = 0; j < nb; j++) {
-                double s = 0.0;
-                for (int k = 0; k < na; k++) s += MA[i * na + k] * T[k * nb + j];
-                D[(size_t)(gp.fa + i) * N + gp.fb + j] = s;
-                if (!same) D[(size_t)(gp.fb + j) * N + gp.fa + i] = s;
-            }
+            ob += kb;
+        }
+        oa += ka;
     }
 }
 

@@ -176,6 +176,7 @@ extern "C" void pimd_scf_opts_default(pimd_scf_opts* o)
     o->guess = 0;
     o->deterministic = 0;
     o->want_gradient = 1;
+    o->use_graphs = 1;
 }
 
 extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
@@ -948,6 +949,59 @@ extern "C" int pimd_sad_atomic_density(pimd_ctx* ctx, const pimd_basis* basis, i
     return PIMD_OK;
 }
 
+// One segment of an SCF iteration's kernel sequence. The first use runs the
+// launches directly (one-time set-up such as tape uploads happens there); the
+// second captures them on the context stream into a CUDA graph, which that
+// and every later use replays. Every argument of the captured launches is a
+// device pointer or a scalar fixed for the whole call (per-iteration values
+// such as build modes, DIIS slots and active masks live in device buffers
+// that the host refreshes between graph launches), so a replay performs
+// exactly the launches of a direct run.
+struct GraphSeg {
+    cudaGraphExec_t exec = nullptr;
+    int uses = 0;
+    long long launches = 0;   // kernel launches of one run, counted on the direct run
+    ~GraphSeg()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+template <class Body>
+static int run_seg(pimd_ctx* ctx, GraphSeg& sg, bool use_graph, Body&& body)
+{
+    const int use = sg.uses++;
+    if (!use_graph || use == 0) {
+        const long long k0 = ctx->stats.kernel_launches;
+        const int rc = body();
+        sg.launches = ctx->stats.kernel_launches - k0;
+        return rc;
+    }
+    if (!sg.exec) {
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const long long k0 = ctx->stats.kernel_launches;
+        const int rc = body();
+        ctx->stats.kernel_launches = k0;
+        const cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+        if (rc || e != cudaSuccess || !gr) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            return rc ? rc : set_err(ctx, PIMD_ECUDA, "CUDA graph capture of an SCF iteration failed");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&sg.exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ei != cudaSuccess) {
+            sg.exec = nullptr;
+            cudaGetLastError();
+            return set_err(ctx, PIMD_ECUDA, "CUDA graph instantiation failed");
+        }
+    }
+    CK(cudaGraphLaunch(sg.exec, ctx->stream));
+    ctx->stats.kernel_launches += sg.launches;
+    return PIMD_OK;
+}
+
 static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc, const double* d_xyz,
                      const pimd_basis* basis, const pimd_scf_opts* o, double* d_E, double* d_grad, pimd_info* info)
 {
@@ -1081,25 +1135,42 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     std::vector<int> mode(nrep, 2), since_full(nrep, 0);
     const int full_every = 8;
     int nactive = nrep;
+    const bool graphs = o->use_graphs != 0;
+    GraphSeg seg_fock, seg_err, seg_diag;
+    if (o->fp32_tau > o->schwarz_tau) {
+        float* Mf;
+        ENSURE("Mf", bt.mtot, Mf);   // allocated before any capture
+    }
+    int *d_mode, *d_slot, *d_count, *d_on;
+    ENSURE("mode", nrep, d_mode);
+    ENSURE("slot", nrep, d_slot);
+    ENSURE("count", nrep, d_count);
+    ENSURE("diis_on", nrep, d_on);
     for (int it = 1; it <= o->max_iter && nactive > 0; it++) {
         for (int r = 0; r < nrep; r++) mode[r] = active[r] ? mode[r] : 0;
-        int* d_mode;
         UPLOAD("mode", mode, d_mode);
         CK(cudaEventRecord(ctx->ev[2], ctx->stream));
-        launch_delta_density(m.rm, nrep, m.D, m.Dp, m.dD, m.G, d_mode, ctx->stream);
-        if ((rc = fock_build(ctx, bt, m, o->schwarz_tau, o->fp32_tau, m.dD))) return rc;
+        rc = run_seg(ctx, seg_fock, graphs, [&]() -> int {
+            launch_delta_density(m.rm, nrep, m.D, m.Dp, m.dD, m.G, d_mode, ctx->stream);
+            ctx->stats.kernel_launches++;
+            return fock_build(ctx, bt, m, o->schwarz_tau, o->fp32_tau, m.dD);
+        });
+        if (rc) return rc;
         CK(cudaEventRecord(ctx->ev[3], ctx->stream));
-        ctx->stats.kernel_launches++;
         ctx->stats.fock_builds++;
-        launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, m.active, ctx->stream);
-        launch_energy(m.rm, nrep, m.D, m.H, m.F, m.enn, m.E, m.active, ctx->stream);
-        gemm(ctx, plan.FD, m.active);
-        gemm(ctx, plan.FDS, m.active);
-        launch_antisym(m.rm, nrep, m.M2, m.Er, m.active, ctx->stream);
-        gemm(ctx, plan.XtE, m.active);
-        gemm(ctx, plan.XtEX, m.active);   // error -> M2
-        launch_maxabs(m.rm, nrep, m.M2, m.emax, m.active, ctx->stream);
-        ctx->stats.kernel_launches += 4;
+        rc = run_seg(ctx, seg_err, graphs, [&]() -> int {
+            launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, m.active, ctx->stream);
+            launch_energy(m.rm, nrep, m.D, m.H, m.F, m.enn, m.E, m.active, ctx->stream);
+            gemm(ctx, plan.FD, m.active);
+            gemm(ctx, plan.FDS, m.active);
+            launch_antisym(m.rm, nrep, m.M2, m.Er, m.active, ctx->stream);
+            gemm(ctx, plan.XtE, m.active);
+            gemm(ctx, plan.XtEX, m.active);   // error -> M2
+            launch_maxabs(m.rm, nrep, m.M2, m.emax, m.active, ctx->stream);
+            ctx->stats.kernel_launches += 4;
+            return PIMD_OK;
+        });
+        if (rc) return rc;
         CK(cudaMemcpyAsync(E.data(), m.E, sizeof(double) * nrep, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaMemcpyAsync(emax.data(), m.emax, sizeof(double) * nrep, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -1154,16 +1225,19 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
                 count[r] = std::min(count[r] + 1, hist);
                 diis_on[r] = count[r] >= 2;
             }
-        int *d_slot, *d_count, *d_on;
         UPLOAD("slot", slot, d_slot);
         UPLOAD("count", count, d_count);
         UPLOAD("diis_on", diis_on, d_on);
-        launch_diis_store(m.rm, nrep, m.F, m.M2, m.Fh, m.Eh, d_slot, hist, m.active, ctx->stream);
-        launch_diis_dots(m.rm, nrep, m.Eh, d_slot, d_count, hist, m.Bd, m.active, ctx->stream);
-        launch_diis_solve(nrep, m.Bd, d_slot, d_count, hist, m.coef, m.active, ctx->stream);
-        launch_diis_combine(m.rm, nrep, m.Fh, m.coef, hist, m.F, m.Fb, d_on, m.active, ctx->stream);
-        ctx->stats.kernel_launches += 4;
-        diag_density(ctx, bt, m, plan, m.active);
+        rc = run_seg(ctx, seg_diag, graphs, [&]() -> int {
+            launch_diis_store(m.rm, nrep, m.F, m.M2, m.Fh, m.Eh, d_slot, hist, m.active, ctx->stream);
+            launch_diis_dots(m.rm, nrep, m.Eh, d_slot, d_count, hist, m.Bd, m.active, ctx->stream);
+            launch_diis_solve(nrep, m.Bd, d_slot, d_count, hist, m.coef, m.active, ctx->stream);
+            launch_diis_combine(m.rm, nrep, m.Fh, m.coef, hist, m.F, m.Fb, d_on, m.active, ctx->stream);
+            ctx->stats.kernel_launches += 4;
+            diag_density(ctx, bt, m, plan, m.active);
+            return PIMD_OK;
+        });
+        if (rc) return rc;
     }
     CK(cudaGetLastError());
     // energies

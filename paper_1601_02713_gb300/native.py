@@ -21,7 +21,7 @@ class PimdScfOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("conv_energy", ctypes.c_double),
                 ("conv_error", ctypes.c_double), ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int),
                 ("schwarz_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("guess", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("want_gradient", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("want_gradient", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class PimdInfo(ctypes.Structure):

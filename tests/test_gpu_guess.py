@@ -265,7 +265,8 @@ def test_save_load_roundtrip(ctx, spd, trained, tmp_path):
     m2.attach(ctx)
     E2, _, i2, _ = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=2))
     assert [i["iterations"] for i in i1] == [i["iterations"] for i in i2]
-    np.testing.assert_array_equal(E1, E2)
+    # the same start: equal to the round-off of the Fock build's atomic accumulation
+    np.testing.assert_allclose(E1, E2, atol=1e-10, rtol=0)
 
 
 def test_learned_guess_errors(ctx, spd):
