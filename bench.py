@@ -324,6 +324,11 @@ def main():
             raise RuntimeError(f"pimd_bo_forces_dev returned {rc}")
         return infos
 
+    # autotuner (not timed): Fock-build tile widths for this workload
+    t_tune = time.perf_counter()
+    widths, tune_ms = native.pimd_autotune(ctx, basis, Z, seq[0].stacked()[1], opts)
+    t_tune = time.perf_counter() - t_tune
+    ctx.clear_guess()
     for i in range(W):
         step(i)
     torch.cuda.synchronize()
@@ -394,6 +399,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nrep * natom * 3 * 8),
                     "d2h_bytes_per_step": int(nrep * 8 + nrep * natom * 3 * 8)},
             "gpu_launches": launches,
+            "autotune": {"tile_widths": widths, "fock_build_ms": tune_ms, "seconds": t_tune,
+                         "note": "ket-tile width per class pair, picked before the warm-up, not timed"},
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, thr, sample, secs = oracle_sample(seq[W], kind, statistics.mean(iters), args.cpu_sample_quartets,

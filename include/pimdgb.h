@@ -274,6 +274,17 @@ int pimd_guess_pair_data(pimd_guess* g, int natom, const int* Z, const double* c
 int pimd_guess_mlp_grad(pimd_guess* g, int n, int type, const float* X, const float* Y, double* loss,
                         float* params_out, float* grads_out);
 
+/* Autotuner (the paper has none: its work distribution is a static MPI
+ * split): times the Fock build of the given replicas (SAD density, the
+ * options' thresholds) once per candidate ket-tile width (32, 64, 128 quartets
+ * per thread block) and keeps, per quartet class pair, the fastest in the
+ * context; later calls on the context build their tiles with those widths.
+ * widths[n] (n = number of class pairs, 21 for s/p/d; may be NULL) receives
+ * the choice and ms_best (may be NULL) the summed time of the chosen widths.
+ * Elements up to Z = 10 (it uses the SAD density). */
+int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords, const pimd_basis* basis,
+                  const pimd_scf_opts* opts, int* widths, double* ms_best);
+
 /* Roofline denominators measured on the device: FP64 FMA, FP32 FMA and FP64
  * tensor-core MMA throughput in TFLOP/s (bounded microbenchmarks, ~1 s). Any
  * output pointer may be NULL. No counterpart in the paper (measurement aid). */

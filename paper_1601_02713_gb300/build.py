@@ -121,7 +121,8 @@ def generate_sources():
             e += _coop_upload_code(nm, False, g)
             e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                   "                     const double* D, const float*, double* G, const double* boys, const float*,",
-                  "                     double tau, double, const double* Dsh, unsigned long long* cnt, cudaStream_t st)",
+                  "                     double tau, double, const double* Dsh, unsigned long long* cnt, int,",
+                  "                     cudaStream_t st)",
                   "{",
                   f"    CoopTape t; int W; size_t bytes;",
                   f"    coop_tape_{nm}(t, W, bytes);",
@@ -132,13 +133,13 @@ def generate_sources():
             e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                   "                     const double* D, const float* Df, double* G, const double* boys,",
                   "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
-                  "                     unsigned long long* cnt, cudaStream_t st)",
+                  "                     unsigned long long* cnt, int bs, cudaStream_t st)",
                   "{",
                   "    if (ntiles <= 0) return;",
                   "    const double split = fp32_tau > tau ? fp32_tau : tau;",
-                  f"    jk_kernel<Cls_{nm}, double><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt);",
+                  f"    jk_kernel<Cls_{nm}, double><<<ntiles, bs, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt);",
                   "    if (fp32_tau > tau)",
-                  f"        jk_kernel<Cls_{nm}, float><<<ntiles, 128, 0, st>>>(P, S, R, tiles, Df, G, boysf, tau, fp32_tau, Dsh,",
+                  f"        jk_kernel<Cls_{nm}, float><<<ntiles, bs, 0, st>>>(P, S, R, tiles, Df, G, boysf, tau, fp32_tau, Dsh,",
                   "                                                        cnt + 2);",
                   "}"]
         if same:
@@ -186,7 +187,7 @@ def generate_sources():
     # dispatch
     d = ['#include "internal.h"', "namespace pimd {"]
     sig_jk = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, const float*, double*, "
-              "const double*, const float*, double, double, const double*, unsigned long long*, cudaStream_t")
+              "const double*, const float*, double, double, const double*, unsigned long long*, int, cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
              "const float*, double, double, const double*, cudaStream_t")
@@ -217,8 +218,13 @@ def generate_sources():
     d.append("static const JkFn jk_tab[] = {" + ", ".join(f"launch_jk_{nm}" for nm in names) + "};")
     d.append("void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau, "
-             "double fp32_tau, const double* Dsh, unsigned long long* cnt, cudaStream_t st)")
-    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, st); }")
+             "double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, cudaStream_t st)")
+    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, bs, st); }")
+    d.append("bool class_pair_coop(int cp)")
+    d.append("{")
+    d.append("    static const bool t[] = {" + ", ".join("true" if coop_e[nm] else "false" for nm in names) + "};")
+    d.append("    return t[cp];")
+    d.append("}")
     same = [nm for c, nm in zip(classes, names) if (c[0], c[1]) == (c[2], c[3])]
     d.append(f"typedef void (*SwFn)({sig_sw});")
     d.append("static const SwFn sw_tab[] = {" + ", ".join(f"launch_schwarz_{nm}" for nm in same) + "};")

@@ -293,7 +293,8 @@ __device__ __forceinline__ void quartet_cart(const R (*sbra)[PIMD_MAXPP], int nb
 
 // Fock (G') build over the quartets of one class pair whose density-weighted
 // Schwarz bound lies in [tau_lo, tau_hi), in precision R (FP64, or FP32 for
-// the small quartets of the mixed mode). blockDim.x == 128.
+// the small quartets of the mixed mode). blockDim.x == the tile's ket width
+// (32, 64 or 128, chosen per class pair by the autotuner).
 // cnt: executed quartets and primitive quartets.
 template <class C, typename R>
 __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, const Tile* __restrict__ tiles,
@@ -305,8 +306,8 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
     const Tile t = tiles[blockIdx.x];
     if (!R_.active[t.rep]) return;
     const int ab = t.ab;
-    if (threadIdx.x < PP_NERI * PIMD_MAXPP) {
-        const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
+    for (int e = threadIdx.x; e < PP_NERI * PIMD_MAXPP; e += blockDim.x) {
+        const int f = e / PIMD_MAXPP, k = e % PIMD_MAXPP;
         sbra[f][k] = pp_base(P, R(0))[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     }
     __syncthreads();

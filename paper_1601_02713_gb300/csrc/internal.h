@@ -52,10 +52,14 @@ void class_pair_ls(int cp, int* la, int* lb, int* lc, int* ld);
 long long class_vrr_flops(int cp);
 // Fock build of one class pair: quartets with bound >= max(tau, fp32_tau) in
 // FP64 (D, boys), those in [tau, fp32_tau) in FP32 (Df, boysf); counters
-// cnt[0..1] FP64 quartets / primitive quartets, cnt[2..3] the same in FP32
+// cnt[0..1] FP64 quartets / primitive quartets, cnt[2..3] the same in FP32;
+// bs = threads per block = the tiles' ket width (the warp-cooperative
+// kernels of the largest classes ignore it)
 void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau,
-               double fp32_tau, const double* Dsh, unsigned long long* cnt, cudaStream_t st);
+               double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, cudaStream_t st);
+// the class pair's Fock build runs on the warp-cooperative tape kernel
+bool class_pair_coop(int cp);
 void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n, const double* boys,
                     double* Q, cudaStream_t st);
 // two-electron gradient of class pair cp: quartets with bound Q_ab Q_cd |Gamma|

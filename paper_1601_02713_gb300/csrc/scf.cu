@@ -103,6 +103,9 @@ struct pimd_ctx {
     cudaEvent_t ev[8];
     int nsm = 152;
     pimd_guess* guess_model = nullptr;   // not owned (guess = 2, 3)
+    // ket width of the quartet tiles per class pair (the Fock-build block
+    // size): 128 until pimd_autotune picks one per class pair
+    int tile_w[64];
     // SAD guess: atomic densities per (basis uid, Z), row-major nbf x nbf
     std::map<std::pair<long long, int>, std::vector<double>> sad;
 };
@@ -190,6 +193,7 @@ extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
     }
     pimd_ctx* ctx = new pimd_ctx();
     ctx->device = device;
+    for (int i = 0; i < 64; i++) ctx->tile_w[i] = 128;
     if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete ctx;
         return PIMD_ECUDA;
@@ -608,6 +612,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     for (int X = 0; X < 6; X++)
         for (int Y = 0; Y <= X; Y++) {
             const int cp = class_pair_index(X, Y);
+            const int tw = ctx->tile_w[cp];
             auto& tl = bt.tiles[cp];
             for (int r = 0; r < nrep; r++) {
                 const int b0 = bt.grp0[r * 6 + X], b1 = bt.grp0[r * 6 + X + 1];
@@ -631,7 +636,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
                             const long long nqi = kend - s0;
                             bt.nq_cp[cp] += nqi;
                             bt.nquart_rep[r] += nqi;
-                            for (int c = s0; c < kend; c += 128) tl.push_back(Tile{i, c, std::min(c + 128, kend), r});
+                            for (int c = s0; c < kend; c += tw) tl.push_back(Tile{i, c, std::min(c + tw, kend), r});
                         }
                         s0 = s1;
                     }
@@ -792,7 +797,7 @@ static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32
     for (int cp = 0; cp < n_class_pairs(); cp++) {
         if (bt.tiles[cp].empty()) continue;
         launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), M, Mf, m.G, ctx->boys, ctx->boysf,
-                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->stream);
+                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->tile_w[cp], ctx->stream);
         ctx->stats.kernel_launches += fp32_tau > tau ? 2 : 1;
     }
     return PIMD_OK;
@@ -1002,6 +1007,37 @@ static int run_seg(pimd_ctx* ctx, GraphSeg& sg, bool use_graph, Body&& body)
     return PIMD_OK;
 }
 
+// block-diagonal D of the cached atomic densities for the replicas in mask
+// (tr(D S) = electrons exactly), into dst; m.dD serves as scratch
+static int sad_place(pimd_ctx* ctx, const pimd_basis* basis, const Batch& bt, Mats& m, const int* Zc,
+                     const std::vector<int>& mask, double* dst)
+{
+    std::vector<double> tab;
+    std::map<int, int> toff;
+    std::vector<int> desc;
+    for (int r = 0; r < bt.nrep; r++) {
+        if (!mask[r]) continue;
+        for (int a = bt.atom0[r]; a < bt.atom0[r + 1]; a++) {
+            const auto& Da = ctx->sad.at({basis->uid, Zc[a]});
+            if (!toff.count(Zc[a])) {
+                toff[Zc[a]] = (int)tab.size();
+                tab.insert(tab.end(), Da.begin(), Da.end());
+            }
+            const int na = (int)lround(sqrt((double)Da.size()));
+            desc.insert(desc.end(), {r, bt.atom_f0[a], na, toff[Zc[a]]});
+        }
+    }
+    double* d_tab;
+    int *d_desc, *d_ms;
+    UPLOAD("sad_tab", tab, d_tab);
+    UPLOAD("sad_desc", desc, d_desc);
+    UPLOAD("mask_sad", mask, d_ms);
+    CK(cudaMemsetAsync(m.dD, 0, sizeof(double) * bt.mtot, ctx->stream));
+    launch_place_blocks(m.rm, d_desc, (int)desc.size() / 4, d_tab, m.dD, ctx->stream);
+    launch_copy_mats(m.rm, bt.nrep, m.dD, dst, d_ms, ctx->stream);
+    return PIMD_OK;
+}
+
 static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc, const double* d_xyz,
                      const pimd_basis* basis, const pimd_scf_opts* o, double* d_E, double* d_grad, pimd_info* info)
 {
@@ -1101,30 +1137,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         ctx->stats.kernel_launches += 19;
     }
     if (nsad > 0) {
-        // block-diagonal D of the atomic densities (tr(D S) = electrons exactly)
-        std::vector<double> tab;
-        std::map<int, int> toff;
-        std::vector<int> desc;
-        for (int r = 0; r < nrep; r++) {
-            if (!sadm[r]) continue;
-            for (int a = bt.atom0[r]; a < bt.atom0[r + 1]; a++) {
-                const auto& Da = ctx->sad.at({basis->uid, Zc[a]});
-                if (!toff.count(Zc[a])) {
-                    toff[Zc[a]] = (int)tab.size();
-                    tab.insert(tab.end(), Da.begin(), Da.end());
-                }
-                const int na = (int)lround(sqrt((double)Da.size()));
-                desc.insert(desc.end(), {r, bt.atom_f0[a], na, toff[Zc[a]]});
-            }
-        }
-        double* d_tab;
-        int *d_desc, *d_ms;
-        UPLOAD("sad_tab", tab, d_tab);
-        UPLOAD("sad_desc", desc, d_desc);
-        UPLOAD("mask_sad", sadm, d_ms);
-        CK(cudaMemsetAsync(m.dD, 0, sizeof(double) * bt.mtot, ctx->stream));
-        launch_place_blocks(m.rm, d_desc, (int)desc.size() / 4, d_tab, m.dD, ctx->stream);
-        launch_copy_mats(m.rm, nrep, m.dD, m.D, d_ms, ctx->stream);
+        if ((rc = sad_place(ctx, basis, bt, m, Zc, sadm, m.D))) return rc;
         ctx->stats.kernel_launches += 2;
     }
     // SCF iterations
@@ -1463,6 +1476,84 @@ extern "C" int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* nato
 // ---------------------------------------------------------------------------
 // testing hooks
 // ---------------------------------------------------------------------------
+// Autotuner: for each class pair, the ket width of the quartet tiles (the
+// Fock-build block size) that builds the Fock matrix of this workload fastest.
+// Candidates 32, 64, 128; each is timed (CUDA events around every class
+// pair's launch, the second of two builds) on a full Fock build of the SAD
+// density of the given replicas with the options' thresholds.
+extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
+                             const pimd_basis* basis, const pimd_scf_opts* opts, int* widths, double* ms_best)
+{
+    pimd_scf_opts o;
+    int rc = check_common(ctx, basis, opts, o);
+    if (rc) return rc;
+    if (nrep <= 0 || natom <= 0 || !Z || !coords) return set_err(ctx, PIMD_EINVAL, "bad sizes or pointers");
+    std::vector<int> nat(nrep, natom), Zc((size_t)nrep * natom);
+    for (int r = 0; r < nrep; r++) std::copy(Z, Z + natom, Zc.begin() + (size_t)r * natom);
+    for (long long i = 0; i < (long long)nrep * natom * 3; i++)
+        if (!std::isfinite(coords[i])) return set_err(ctx, PIMD_EINVAL, "non-finite coordinates");
+    if ((rc = sad_ensure(ctx, basis, Zc.data(), nrep * natom))) return rc;
+    double* d_xyz;
+    ENSURE("xyz", (size_t)nrep * natom * 3, d_xyz);
+    CK(cudaMemcpyAsync(d_xyz, coords, sizeof(double) * nrep * natom * 3, cudaMemcpyHostToDevice, ctx->stream));
+    const int ncp = n_class_pairs();
+    const int cand[3] = {32, 64, 128};
+    std::vector<double> ms((size_t)ncp * 3, 0.0);
+    std::vector<cudaEvent_t> ev(2 * (size_t)ncp);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    int rc2 = PIMD_OK;
+    for (int ci = 0; ci < 3 && !rc2; ci++) {
+        for (int cp = 0; cp < ncp; cp++) ctx->tile_w[cp] = cand[ci];
+        Batch bt;
+        if ((rc2 = setup_batch(ctx, bt, nrep, nat.data(), Zc.data(), d_xyz, basis, o.schwarz_tau))) break;
+        Mats m;
+        if ((rc2 = alloc_mats(ctx, bt, m, 2))) break;
+        std::vector<int> active(nrep, 1);
+        if ((rc2 = upload(ctx, "active", active, &m.active))) break;
+        bt.R.active = m.active;
+        if ((rc2 = sad_place(ctx, basis, bt, m, Zc.data(), active, m.D))) break;
+        float* Mf = nullptr;
+        if (o.fp32_tau > o.schwarz_tau) {
+            if ((rc2 = dev_ensure(ctx, "Mf", (size_t)bt.mtot, &Mf))) break;
+        }
+        for (int pass = 0; pass < 2 && !rc2; pass++) {
+            cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream);
+            launch_shell_bounds(bt.S, bt.R, bt.nrep, bt.maxsh, m.D, bt.Dsh, bt.R.active, ctx->stream);
+            if (Mf) launch_to_float(m.D, Mf, bt.mtot, ctx->stream);
+            for (int cp = 0; cp < ncp; cp++) {
+                cudaEventRecord(ev[2 * cp], ctx->stream);
+                if (!bt.tiles[cp].empty())
+                    launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, Mf, m.G, ctx->boys,
+                              ctx->boysf, o.schwarz_tau, o.fp32_tau, bt.Dsh, bt.cnt + 4 * cp, cand[ci], ctx->stream);
+                cudaEventRecord(ev[2 * cp + 1], ctx->stream);
+            }
+            if (cudaStreamSynchronize(ctx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+                rc2 = set_err(ctx, PIMD_ECUDA, "autotune: Fock build failed");
+                break;
+            }
+            if (pass == 1)
+                for (int cp = 0; cp < ncp; cp++) {
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, ev[2 * cp], ev[2 * cp + 1]);
+                    ms[(size_t)cp * 3 + ci] = t;
+                }
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    double best = 0.0;
+    for (int cp = 0; cp < ncp; cp++) {
+        int bi = 2;
+        if (!rc2)
+            for (int ci = 0; ci < 3; ci++)
+                if (ms[(size_t)cp * 3 + ci] < ms[(size_t)cp * 3 + bi]) bi = ci;
+        ctx->tile_w[cp] = cand[bi];
+        best += ms[(size_t)cp * 3 + bi];
+        if (widths) widths[cp] = cand[bi];
+    }
+    if (ms_best) *ms_best = best;
+    return rc2;
+}
+
 extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
                              const pimd_basis* basis, double schwarz_tau, double fp32_tau, const double* D_dev,
                              double* G_dev)

@@ -106,6 +106,7 @@ def load(path: str | None = None):
                                          _LL, _F, _D, _F, _D]
     lib.pimd_guess_mlp_grad.argtypes = [_P, ctypes.c_int, ctypes.c_int, _F, _F, _D, _F, _F]
     lib.pimd_sad_atomic_density.argtypes = [_P, _P, ctypes.c_int, _D, ctypes.c_int]
+    lib.pimd_autotune.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.POINTER(PimdScfOpts), _I, _D]
     lib.pimd_strerror.argtypes = [ctypes.c_int]
     lib.pimd_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -289,6 +290,19 @@ def pimd_sad_atomic_density(ctx: Context, basis: Basis, Z: int):
     D = np.zeros((n, n))
     _check(load().pimd_sad_atomic_density(ctx.handle, basis.handle, int(Z), _dp(D), n), "pimd_sad_atomic_density")
     return D
+
+
+def pimd_autotune(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | None = None):
+    """Pick the Fock-build tile width per class pair for this workload;
+    returns (widths [21], ms of one build with them)."""
+    Z = np.ascontiguousarray(Z, np.int32)
+    X = np.ascontiguousarray(coords, np.float64)
+    opts = opts or scf_opts()
+    w = np.zeros(64, np.int32)
+    ms = np.zeros(1)
+    _check(load().pimd_autotune(ctx.handle, X.shape[0], X.shape[1], _ip(Z), _dp(X), basis.handle,
+                                ctypes.byref(opts), _ip(w), _dp(ms)), "pimd_autotune")
+    return w[:21].tolist(), float(ms[0])
 
 
 def pimd_last_stats(ctx: Context) -> dict:

@@ -257,3 +257,36 @@ def test_water32_full_size_sampled_fock_blocks(ctx, spd, fp32_tau, tol):
         got = G[off[a]:off[a + 1], off[b]:off[b + 1]]
         err = np.abs(got - ref).max()
         assert err < tol * max(1.0, np.abs(ref).max()), (a, b, err)
+
+
+def test_autotune_keeps_results(spd):
+    """Tile widths picked by the autotuner change the work decomposition
+    only: energies and gradients stay within round-off."""
+    bas, B = spd
+    c = native.Context(0)
+    r, _ = inputs.workload("water8_spd_32beads", nrep=2)
+    Z, X = r.stacked()
+    E0, G0, _, _ = native.pimd_bo_forces(c, B, Z, X)
+    widths, ms = native.pimd_autotune(c, B, Z, X)
+    assert len(widths) == 21 and all(w in (32, 64, 128) for w in widths) and ms > 0
+    c.clear_guess()
+    E1, G1, info, _ = native.pimd_bo_forces(c, B, Z, X)
+    assert all(i["converged"] for i in info)
+    np.testing.assert_allclose(E1, E0, atol=1e-10, rtol=0)
+    np.testing.assert_allclose(G1, G0, atol=1e-9, rtol=0)
+    c.close()
+
+
+def test_graph_replay_matches_plain_launches(ctx, spd):
+    """use_graphs = 0 (plain launches) and 1 (CUDA graphs from the second SCF
+    iteration on) give the same energies, gradients and iteration counts."""
+    bas, B = spd
+    r, _ = inputs.workload("water8_spd_32beads", nrep=3)
+    Z, X = r.stacked()
+    ctx.clear_guess()
+    E0, G0, i0, _ = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(use_graphs=0))
+    ctx.clear_guess()
+    E1, G1, i1, _ = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(use_graphs=1))
+    assert [i["iterations"] for i in i0] == [i["iterations"] for i in i1]
+    np.testing.assert_allclose(E1, E0, atol=1e-10, rtol=0)
+    np.testing.assert_allclose(G1, G0, atol=1e-9, rtol=0)
