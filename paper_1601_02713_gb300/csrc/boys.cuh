@@ -12,7 +12,12 @@
 // stable for all T. T >= BOYS_TMAX: F_0 = (1/2) sqrt(pi / T) (erf of sqrt(T)
 // is 1 in double precision there) and the upward recursion
 //   F_{m+1} = ((2m + 1) F_m - e^{-T}) / (2T),
-// stable because 2T > 2m + 1 for every order used here.
+// stable because 2T > 2m + 1 for every order used here. There e^{-T} is at
+// most 3e-7 of (2m + 1) F_m (T >= 40, m <= 12), so it is needed only to about
+// 1e-10 relative: e^{-T_k} from the table times a fourth-order series of
+// e^{T_k - T} (truncation 2.5e-10). From T = BOYS_TEXP on it is below half an
+// ulp of (2m + 1) F_m for every order up to 13 (checked against 40-digit
+// quadrature) and is dropped.
 // The tables are filled on the host by `boys_fill_table` (series in long double).
 #pragma once
 #include <cuda_runtime.h>
@@ -23,8 +28,12 @@
 #define BOYS_MMAX 12          // highest order any kernel asks for
 #define BOYS_NTAYLOR 8        // Taylor terms
 #define BOYS_MT (BOYS_MMAX + 1)
-// table layout: [BOYS_NT][BOYS_MT][BOYS_NTAYLOR] F_{m+j}(T_k)/j!, then [BOYS_NT] e^{-T_k}
-#define BOYS_TAB_DOUBLES (BOYS_NT * BOYS_MT * BOYS_NTAYLOR + BOYS_NT)
+#define BOYS_TEXP 72.0        // e^{-T} dropped from here on
+#define BOYS_NE (72 * BOYS_GRID + 1)
+// table layout: [BOYS_NT][BOYS_MT][BOYS_NTAYLOR] F_{m+j}(T_k)/j!, then
+// [BOYS_NE] e^{-T_k} (T_k = k / BOYS_GRID up to BOYS_TEXP)
+#define BOYS_EXP_OFF (BOYS_NT * BOYS_MT * BOYS_NTAYLOR)
+#define BOYS_TAB_DOUBLES (BOYS_EXP_OFF + BOYS_NE)
 
 // FP32 table for the mixed-precision quartets: [BOYS_NT][BOYS_MT][4]
 // F_{m+j}(T_k)/j! then [BOYS_NT] e^{-T_k} (4 Taylor terms: truncation below
@@ -50,11 +59,25 @@ __device__ __forceinline__ double exp_poly(double x)
     return fma(e, x, 1.0);
 }
 
+// theta e^{-T} for BOYS_TMAX <= T (the asymptotic branch), 0 from BOYS_TEXP on
+__device__ __forceinline__ double boys_exp_tail(double T, const double* __restrict__ tab, double theta)
+{
+    if (T >= BOYS_TEXP) return 0.0;
+    const int k = __double2int_rn(T * BOYS_GRID);
+    const double x = k * (1.0 / BOYS_GRID) - T;
+    double e = 1.0 / 24.0;
+    e = fma(e, x, 1.0 / 6.0);
+    e = fma(e, x, 0.5);
+    e = fma(e, x, 1.0);
+    e = fma(e, x, 1.0);
+    return theta * __ldg(tab + BOYS_EXP_OFF + k) * e;
+}
+
 // F[m] = theta F_m(T), m = 0..L (L a compile-time order)
 template <int L>
 __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double theta, double* F)
 {
-    constexpr double kPi = 3.14159265358979323846;
+    constexpr double kHalfSqrtPi = 0.88622692545275801365;   // sqrt(pi) / 2
     if (T < BOYS_TMAX) {
         const int k = __double2int_rn(T * BOYS_GRID);
         const double x = k * (1.0 / BOYS_GRID) - T;
@@ -70,11 +93,11 @@ __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ t
             for (int m = L - 1; m >= 0; m--) F[m] = fma(t2, F[m + 1], te) * (1.0 / (2 * m + 1));
         }
     } else {
-        const double it = 1.0 / T;
-        F[0] = theta * 0.5 * sqrt(kPi * it);
+        const double rs = rsqrt(T);
+        F[0] = theta * kHalfSqrtPi * rs;
         if (L > 0) {
-            const double te = theta * exp(-T);
-            const double h = 0.5 * it;
+            const double te = boys_exp_tail(T, tab, theta);
+            const double h = 0.5 * rs * rs;
 #pragma unroll
             for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - te) * h;
         }
@@ -117,7 +140,7 @@ __device__ __forceinline__ void boys_eval(float T, const float* __restrict__ tab
 // runtime-order version (one-electron integrals, tape kernels)
 __device__ __forceinline__ void boys_eval_n(int L, double T, const double* __restrict__ tab, double theta, double* F)
 {
-    constexpr double kPi = 3.14159265358979323846;
+    constexpr double kHalfSqrtPi = 0.88622692545275801365;   // sqrt(pi) / 2
     if (T < BOYS_TMAX) {
         const int k = __double2int_rn(T * BOYS_GRID);
         const double x = k * (1.0 / BOYS_GRID) - T;
@@ -132,11 +155,11 @@ __device__ __forceinline__ void boys_eval_n(int L, double T, const double* __res
             for (int m = L - 1; m >= 0; m--) F[m] = fma(t2, F[m + 1], te) / (2 * m + 1);
         }
     } else {
-        const double it = 1.0 / T;
-        F[0] = theta * 0.5 * sqrt(kPi * it);
+        const double rs = rsqrt(T);
+        F[0] = theta * kHalfSqrtPi * rs;
         if (L > 0) {
-            const double te = theta * exp(-T);
-            const double h = 0.5 * it;
+            const double te = boys_exp_tail(T, tab, theta);
+            const double h = 0.5 * rs * rs;
             for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - te) * h;
         }
     }

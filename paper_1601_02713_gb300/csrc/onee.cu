@@ -674,8 +674,8 @@ void boys_fill_table(double* tab)
             for (int m = 0; m < BOYS_MT; m++)
                 tab[((size_t)k * BOYS_MT + m) * BOYS_NTAYLOR + j] = (double)(F[m + j] / fact);
         }
-        tab[(size_t)BOYS_NT * BOYS_MT * BOYS_NTAYLOR + k] = (double)expl(-T);
     }
+    for (int k = 0; k < BOYS_NE; k++) tab[BOYS_EXP_OFF + k] = (double)expl(-(long double)k / BOYS_GRID);
 }
 
 void boys_table_upload(double** dev_tab, float** dev_tabf)
