@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* __restrict__ 
 // g_p <- c g_p - s g_q, g_q <- s g_p + c g_q.
 // ---------------------------------------------------------------------------
 constexpr int JAC_THREADS = 512;
-constexpr int JAC_PER = 24;   // column elements per lane: n <= 768
+constexpr int JAC_PER = 24;   // largest column length per lane: n <= 768
 constexpr int JAC_MAXSWEEP = 60;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -91,6 +91,10 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// PER = column elements held per lane (n <= 32 PER): the kernel is FP64-bound
+// on one SM per matrix, so PER is the smallest instantiated length that fits
+// the batch's largest matrix (padding lanes would be FP64 work on zeros).
+template <int PER>
 __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __restrict__ rms, const double* A,
                                                              double* V, double* evals, int ldE, double* work,
                                                              const int* active, int shift_to_spd)
@@ -151,16 +155,16 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
                 double* gp = G + (size_t)p * n;
                 double* gq = G + (size_t)q * n;
                 // both columns in registers (all loads in flight at once)
-                double x[JAC_PER], y[JAC_PER];
+                double x[PER], y[PER];
 #pragma unroll
-                for (int k = 0; k < JAC_PER; k++) {
+                for (int k = 0; k < PER; k++) {
                     const int i = lane + 32 * k;
                     x[k] = i < n ? gp[i] : 0.0;
                     y[k] = i < n ? gq[i] : 0.0;
                 }
                 double al = 0.0, be = 0.0, ga = 0.0;
 #pragma unroll
-                for (int k = 0; k < JAC_PER; k++) {
+                for (int k = 0; k < PER; k++) {
                     al = fma(x[k], x[k], al);
                     be = fma(y[k], y[k], be);
                     ga = fma(x[k], y[k], ga);
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
                     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
 #pragma unroll
-                    for (int k = 0; k < JAC_PER; k++) {
+                    for (int k = 0; k < PER; k++) {
                         const int i = lane + 32 * k;
                         if (i < n) {
                             gp[i] = c * x[k] - s * y[k];
@@ -209,6 +213,27 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
         const double inv = lj > 0.0 ? 1.0 / lj : 0.0;
         for (int i = 0; i < n; i++) v[(size_t)i * n + rank] = G[(size_t)j * n + i] * inv;
     }
+}
+
+// one block per matrix; nmax = the largest n of the batch (<= 32 JAC_PER)
+static void jacobi_dispatch(int nmat, int nmax, cudaStream_t st, const RepMat* rm, const double* A, double* V,
+                            double* evals, int ldE, double* work, const int* active, int shift)
+{
+    const size_t sm = sizeof(double) * nmax;
+    if (nmax <= 32 * 2)
+        jacobi_kernel<2><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+    else if (nmax <= 32 * 4)
+        jacobi_kernel<4><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+    else if (nmax <= 32 * 6)
+        jacobi_kernel<6><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+    else if (nmax <= 32 * 8)
+        jacobi_kernel<8><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+    else if (nmax <= 32 * 12)
+        jacobi_kernel<12><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+    else if (nmax <= 32 * 16)
+        jacobi_kernel<16><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+    else
+        jacobi_kernel<JAC_PER><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
 }
 
 __global__ void fock_assemble_kernel(const RepMat* rms, const double* h, const double* G, double* F,
@@ -568,8 +593,7 @@ void launch_jacobi(const RepMat* d_rm, int nrep, const double* A, double* V, dou
     // ldE is the largest n of the batch; the kernel holds 32 * JAC_PER column elements per warp
     if (ldE > 32 * JAC_PER) return;
     if (nrep == 0) return;
-    jacobi_kernel<<<nrep, JAC_THREADS, sizeof(double) * ldE, st>>>(d_rm, A, V, evals, ldE, work, active,
-                                                                  shift_to_spd);
+    jacobi_dispatch(nrep, ldE, st, d_rm, A, V, evals, ldE, work, active, shift_to_spd);
 }
 
 static dim3 elem_grid(int nrep) { return dim3(64, nrep); }
@@ -679,8 +703,7 @@ int eigh_noalloc(int nmat, int n, const double* A, double* V, double* evals, cud
     for (int r = 0; r < nmat; r++) hd[r] = RepMat{n, 0, (long long)r * n * n};
     if (cudaMemcpyAsync(g_eigh_desc_ptr[dev], hd, sizeof(RepMat) * nmat, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return -3;
-    jacobi_kernel<<<nmat, JAC_THREADS, sizeof(double) * n, st>>>(g_eigh_desc_ptr[dev], A, V, evals, n,
-                                                                 g_eigh_work_ptr[dev], nullptr, 1);
+    jacobi_dispatch(nmat, n, st, g_eigh_desc_ptr[dev], A, V, evals, n, g_eigh_work_ptr[dev], nullptr, 1);
     if (cudaGetLastError() != cudaSuccess) return -3;
     if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
     return 0;
