@@ -273,6 +273,13 @@ int pimd_guess_pair_data(pimd_guess* g, int natom, const int* Z, const double* c
                          long long* block_off, float* feats, double* frames, float* local_out, double* D_out);
 int pimd_guess_mlp_grad(pimd_guess* g, int n, int type, const float* X, const float* Y, double* loss,
                         float* params_out, float* grads_out);
+/* pimd_bf16_gemm_dev: the network's GEMM alone, C[M][N] (float, device) =
+ *   op(A) op(B) with bf16 device matrices A, B (row-major, leading dimensions
+ *   lda, ldb; ta / tb = 1 reads the transpose), FP32 accumulation; impl 0 is the
+ *   5th-generation tensor-core (tcgen05, TMEM accumulator) kernel the network
+ *   uses, 1 the mma.sync kernel. PIMD_ETIMEOUT if a bounded wait expired. */
+int pimd_bf16_gemm_dev(int M, int N, int K, const void* A, int lda, int ta, const void* B, int ldb, int tb, float* C,
+                       int ldc, int impl, void* stream);
 
 /* Autotuner (the paper has none: its work distribution is a static MPI
  * split): times the Fock build of the given replicas (SAD density, the

@@ -32,6 +32,7 @@
 
 #include "../../include/pimdgb.h"
 #include "internal.h"
+#include "umma_gemm.cuh"
 
 namespace pimd {
 
@@ -1035,6 +1036,30 @@ extern "C" int pimd_guess_pair_data(pimd_guess* g, int natom, const int* Z, cons
     if (feats) cudaMemcpy(feats, Xf, sizeof(float) * (size_t)n * G_NF, cudaMemcpyDeviceToHost);
     if (frames) cudaMemcpy(frames, wk.frames, sizeof(double) * (size_t)n * 9, cudaMemcpyDeviceToHost);
     return cudaGetLastError() == cudaSuccess ? PIMD_OK : PIMD_ECUDA;
+}
+
+// BF16 GEMM test hook: impl 0 = the tcgen05 kernel, 1 = the mma.sync kernel
+extern "C" int pimd_bf16_gemm_dev(int M, int N, int K, const void* A, int lda, int ta, const void* B, int ldb, int tb,
+                                  float* C, int ldc, int impl, void* stream)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (impl != 0 && impl != 1)) return PIMD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (impl == 1) {
+        gemm_bf16(M, N, K, (const __nv_bfloat16*)A, lda, ta, (const __nv_bfloat16*)B, ldb, tb, C, ldc, 0.f, st);
+        return cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess ? PIMD_OK : PIMD_ECUDA;
+    }
+    int* d_err;
+    if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return PIMD_ENOMEM;
+    cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    dim3 grid((N + UMMA_N - 1) / UMMA_N, (M + UMMA_M - 1) / UMMA_M);
+    bf16_gemm_tc_kernel<<<grid, 128, 0, st>>>(M, N, K, (const __nv_bfloat16*)A, lda, ta, (const __nv_bfloat16*)B, ldb,
+                                              tb, C, ldc, d_err);
+    int h_err = 0;
+    const bool fine = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                      cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    cudaFree(d_err);
+    if (!fine) return PIMD_ECUDA;
+    return h_err ? PIMD_ETIMEOUT : PIMD_OK;
 }
 
 // ---------------------------------------------------------------- save / load

@@ -107,6 +107,8 @@ def load(path: str | None = None):
     lib.pimd_guess_mlp_grad.argtypes = [_P, ctypes.c_int, ctypes.c_int, _F, _F, _D, _F, _F]
     lib.pimd_sad_atomic_density.argtypes = [_P, _P, ctypes.c_int, _D, ctypes.c_int]
     lib.pimd_autotune.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.POINTER(PimdScfOpts), _I, _D]
+    lib.pimd_bf16_gemm_dev.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
+                                       ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P]
     lib.pimd_strerror.argtypes = [ctypes.c_int]
     lib.pimd_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -303,6 +305,16 @@ def pimd_autotune(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | Non
     _check(load().pimd_autotune(ctx.handle, X.shape[0], X.shape[1], _ip(Z), _dp(X), basis.handle,
                                 ctypes.byref(opts), _ip(w), _dp(ms)), "pimd_autotune")
     return w[:21].tolist(), float(ms[0])
+
+
+def pimd_bf16_gemm_dev(A, B, C, ta: bool, tb: bool, impl: int = 0, stream: int = 0) -> int:
+    """C = op(A) op(B) for bf16 CUDA tensors A, B (row-major) into the float32
+    CUDA tensor C [M, N]; returns the status code."""
+    M, N = int(C.shape[0]), int(C.shape[1])
+    K = int(A.shape[0] if ta else A.shape[1])
+    return load().pimd_bf16_gemm_dev(M, N, K, _P(A.data_ptr()), int(A.stride(0)), int(ta), _P(B.data_ptr()),
+                                     int(B.stride(0)), int(tb), _P(C.data_ptr()), int(C.stride(0)), int(impl),
+                                     _P(stream))
 
 
 def pimd_last_stats(ctx: Context) -> dict:
