@@ -40,6 +40,9 @@ UNIT = "bead evals/s"
 # FP64 pipe of GB300: 4 FP64 flops per clock per SM (2 FMA; the FMA-chain
 # microbenchmark measured 1.255 TFLOP/s), 152 SMs, 2.07 GHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# FP32 pipe: 128 FP32 lanes x 2 flops (FMA) per clock per SM (the FMA-chain
+# microbenchmark measured 76.7 TFLOP/s)
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
 
 
 def parse():
@@ -369,6 +372,7 @@ def main():
     fock_ms = sum(s["ms_fock"] for s in stats)
     builds = sum(s["fock_builds"] for s in stats)
     flops = sum(s["eri_flops_per_build"] * s["fock_builds"] for s in stats)
+    flops32 = sum(s["eri_flops32_per_build"] * s["fock_builds"] for s in stats)
     eris = sum(s["eris_per_build"] * s["fock_builds"] for s in stats)
     achieved = flops / (fock_ms * 1e-3) / 1e12
     geri = eris / (fock_ms * 1e-3) / 1e9
@@ -394,6 +398,11 @@ def main():
             "roofline": {"kernel": "jk_kernel (one Fock build = all quartet classes)", "bound": "alu",
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "fp32_achieved": flops32 / (fock_ms * 1e-3) / 1e12,
+                         "fp32_frac": flops32 / (fock_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "note": ("achieved/frac: FP64 operations of the Fock build over its time against the FP64 "
+                                  "pipe; fp32_*: the FP32 quartets' operations over the same time against the FP32 "
+                                  "pipe (mixed mode); their sum is the share of the two pipes' peak the build uses"),
                          "flops_per_launch": flops / max(builds, 1), "ms_per_launch": fock_ms / max(builds, 1),
                          "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (FMA chain measured 1.255)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nrep * natom * 3 * 8),

@@ -57,25 +57,29 @@ def _write(path, text):
 
 
 def _coop_upload_code(nm, grad, g):
-    """C++ lines defining coop_tape_<nm>(CoopTape&, int& warps, size_t& smem):
-    uploads the class's tape once per device and sizes the launch."""
+    """C++ lines defining coop_tape_<nm>(CoopTape&, int& W, size_t& bytes,
+    int& Wf, size_t& bytesf): uploads the class's tape once per device and
+    sizes the FP64 and FP32 launches (warps per block, shared memory)."""
     pre = f"coop{'g' if grad else 'e'}_{nm}"
     st = f"Coop{'G' if grad else 'E'}_{nm}"
     c = [cl for cl in g.classes() if g.cls_name(cl) == nm][0]
     hr = g.grad_hrrs(c) if grad else [("E", c, "acc")]
     la, lb, lc, ld = c
     nc4 = g.ncart(la) * g.ncart(lb) * g.ncart(lc) * g.ncart(ld)
-    kernel = (f"grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}>" if grad else f"jk_coop_kernel<{la}, {lb}, {lc}, {ld}>")
+    kernel = (f"grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}" if grad else f"jk_coop_kernel<{la}, {lb}, {lc}, {ld}")
     lines = ["static CoopTape g_coop[64];", "static bool g_coop_up[64];",
              "template <typename T> static const T* coop_copy(const T* h, size_t n)",
              "{", "    T* d = nullptr;", "    cudaMalloc(&d, n * sizeof(T));",
              "    cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice);", "    return d;", "}",
-             f"static void coop_tape_{nm}(CoopTape& t, int& W, size_t& bytes)", "{",
+             f"static void coop_tape_{nm}(CoopTape& t, int& W, size_t& bytes, int& Wf, size_t& bytesf)", "{",
              "    int dev = 0;", "    cudaGetDevice(&dev);",
              f"    const int per = coop_warp_doubles({st}::NACC, {st}::NWORK, {st}::L, {nc4});",
              "    W = (int)(220 * 1024 / (per * sizeof(double)));",
              "    W = W < 1 ? 1 : (W > 4 ? 4 : W);",
              "    bytes = (size_t)W * per * sizeof(double);",
+             "    Wf = (int)(220 * 1024 / (per * sizeof(float)));",
+             "    Wf = Wf < 1 ? 1 : (Wf > 4 ? 4 : Wf);",
+             "    bytesf = (size_t)Wf * per * sizeof(float);",
              "    if (dev >= 0 && dev < 64 && !g_coop_up[dev]) {",
              "        CoopTape c{};",
              f"        c.vrr = coop_copy({pre}_vrr, sizeof({pre}_vrr) / sizeof(int));",
@@ -94,7 +98,8 @@ def _coop_upload_code(nm, grad, g):
                   f"        c.out[{k}] = coop_copy({pre}_out{hname}, sizeof({pre}_out{hname}) / sizeof(int));",
                   f"        c.hpos[{k}] = {pos};", f"        c.hup[{k}] = {up};"]
     lines += ["        g_coop[dev] = c;", "        g_coop_up[dev] = true;",
-              f"        cudaFuncSetAttribute({kernel}, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);",
+              f"        cudaFuncSetAttribute({kernel}, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);",
+              f"        cudaFuncSetAttribute({kernel}, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytesf);",
               "    }", "    t = g_coop[dev];", "}"]
     return lines
 
@@ -120,14 +125,19 @@ def generate_sources():
         if coop_e[nm]:
             e += _coop_upload_code(nm, False, g)
             e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                  "                     const double* D, const float*, double* G, const double* boys, const float*,",
-                  "                     double tau, double, const double* Dsh, unsigned long long* cnt, int,",
-                  "                     cudaStream_t st)",
+                  "                     const double* D, const float* Df, double* G, const double* boys,",
+                  "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
+                  "                     unsigned long long* cnt, int, cudaStream_t st)",
                   "{",
-                  f"    CoopTape t; int W; size_t bytes;",
-                  f"    coop_tape_{nm}(t, W, bytes);",
-                  f"    if (ntiles > 0) jk_coop_kernel<{la}, {lb}, {lc}, {ld}><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles, D,",
-                  "        G, boys, tau, Dsh, cnt, t);",
+                  "    if (ntiles <= 0) return;",
+                  "    CoopTape t; int W, Wf; size_t bytes, bytesf;",
+                  f"    coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
+                  "    const double split = fp32_tau > tau ? fp32_tau : tau;",
+                  f"    jk_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles, D,",
+                  "        G, boys, split, 1e300, Dsh, cnt, t);",
+                  "    if (fp32_tau > tau)",
+                  f"        jk_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S, R, tiles,",
+                  "            Df, G, boysf, tau, fp32_tau, Dsh, cnt + 2, t);",
                   "}"]
         else:
             e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
@@ -170,15 +180,20 @@ def generate_sources():
                    "}"]
         else:
             gl += _coop_upload_code(nm, True, g)
-            gl += [f"void grad2e_upload_{nm}() {{ CoopTape t; int W; size_t b; coop_tape_{nm}(t, W, b); }}",
+            gl += [f"void grad2e_upload_{nm}() {{ CoopTape t; int W, Wf; size_t b, bf; coop_tape_{nm}(t, W, b, Wf, bf); }}",
                    f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                   "                        const double* D, double* grad, const double* boys, const float*, double tau,",
-                   "                        double, const double* Dsh, cudaStream_t st)",
+                   "                        const double* D, double* grad, const double* boys, const float* boysf,",
+                   "                        double tau, double fp32_tau, const double* Dsh, cudaStream_t st)",
                    "{",
-                   "    CoopTape t; int W; size_t bytes;",
-                   f"    coop_tape_{nm}(t, W, bytes);",
-                   f"    if (ntiles > 0) grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles,",
-                   "        D, grad, boys, tau, Dsh, t);",
+                   "    if (ntiles <= 0) return;",
+                   "    CoopTape t; int W, Wf; size_t bytes, bytesf;",
+                   f"    coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
+                   "    const double split = fp32_tau > tau ? fp32_tau : tau;",
+                   f"    grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles,",
+                   "        D, grad, boys, split, 1e300, Dsh, t);",
+                   "    if (fp32_tau > tau)",
+                   f"        grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S, R,",
+                   "            tiles, D, grad, boysf, tau, fp32_tau, Dsh, t);",
                    "}"]
         gl.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_grad_{nm}.cu")

@@ -137,6 +137,36 @@ __device__ __forceinline__ void boys_eval(float T, const float* __restrict__ tab
     }
 }
 
+// runtime-order FP32 version (tape kernels of the mixed-precision quartets)
+__device__ __forceinline__ void boys_eval_n(int L, float T, const float* __restrict__ tab, float theta, float* F)
+{
+    constexpr float kPi = 3.14159265358979f;
+    if (T < (float)BOYS_TMAX) {
+        const int k = __float2int_rn(T * BOYS_GRID);
+        const float x = k * (1.0f / BOYS_GRID) - T;
+        const float* t = tab + ((size_t)k * BOYS_MT + L) * BOYS_NTAYLOR_F;
+        float f = __ldg(t + 3);
+        f = fmaf(f, x, __ldg(t + 2));
+        f = fmaf(f, x, __ldg(t + 1));
+        f = fmaf(f, x, __ldg(t));
+        F[L] = theta * f;
+        if (L > 0) {
+            const float ex = fmaf(fmaf(fmaf(1.0f / 6.0f, x, 0.5f), x, 1.0f), x, 1.0f);
+            const float te = theta * __ldg(tab + BOYS_NT * BOYS_MT * BOYS_NTAYLOR_F + k) * ex;
+            const float t2 = 2.0f * T;
+            for (int m = L - 1; m >= 0; m--) F[m] = fmaf(t2, F[m + 1], te) / (float)(2 * m + 1);
+        }
+    } else {
+        const float it = 1.0f / T;
+        F[0] = theta * 0.5f * sqrtf(kPi * it);
+        if (L > 0) {
+            const float te = theta * __expf(-T);
+            const float h = 0.5f * it;
+            for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - te) * h;
+        }
+    }
+}
+
 // runtime-order version (one-electron integrals, tape kernels)
 __device__ __forceinline__ void boys_eval_n(int L, double T, const double* __restrict__ tab, double theta, double* F)
 {

@@ -7,6 +7,9 @@
 // of a level in parallel, with a __syncwarp between levels. The primitive
 // quartets' geometric factors and Boys values are computed 32 at a time, one
 // per lane. A block holds several warps, each on its own quartet of the tile.
+// Templated on the arithmetic precision R: FP64, or FP32 for the small
+// quartets of the mixed mode (pair data, Boys table and density in FP32; the
+// Fock matrix and the gradient accumulate in FP64).
 #pragma once
 #include "grad_kernels.cuh"
 
@@ -24,7 +27,8 @@ struct CoopTape {
     int L, NACC, F0, NWORK;
 };
 
-__device__ __forceinline__ double warp_sum_d(double v)
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -35,14 +39,16 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // o2qr, o2pq (5), 2a, 2b, 2c (3), then F_m * theta (L + 1)
 constexpr int COOP_NG0 = 20;
 
-__device__ __forceinline__ double sel3(int d, const double* v) { return d == 0 ? v[0] : (d == 1 ? v[1] : v[2]); }
+template <typename R>
+__device__ __forceinline__ R sel3(int d, const R* v) { return d == 0 ? v[0] : (d == 1 ? v[1] : v[2]); }
 
 // run the level-sorted VRR of one primitive quartet (geometry g) in sm
-__device__ __forceinline__ void coop_vrr(const CoopTape& tp, double* sm, const double* g, int lane)
+template <typename R>
+__device__ __forceinline__ void coop_vrr(const CoopTape& tp, R* sm, const R* g, int lane)
 {
-    double PA[3] = {g[0], g[1], g[2]}, WP[3] = {g[3], g[4], g[5]}, QC[3] = {g[6], g[7], g[8]},
-           WQ[3] = {g[9], g[10], g[11]};
-    const double o2p = g[12], o2pr = g[13], o2q = g[14], o2qr = g[15], o2pq = g[16];
+    R PA[3] = {g[0], g[1], g[2]}, WP[3] = {g[3], g[4], g[5]}, QC[3] = {g[6], g[7], g[8]},
+      WQ[3] = {g[9], g[10], g[11]};
+    const R o2p = g[12], o2pr = g[13], o2q = g[14], o2qr = g[15], o2pq = g[16];
     for (int lv = 0; lv < tp.nvlev; lv++) {
         const int hi = __ldg(tp.vrr_lv + lv + 1);
         for (int o = __ldg(tp.vrr_lv + lv) + lane; o < hi; o += 32) {
@@ -50,7 +56,7 @@ __device__ __forceinline__ void coop_vrr(const CoopTape& tp, double* sm, const d
             const int4 b = __ldg((const int4*)(tp.vrr + 8 * o + 4));
             // a = {kind, dst, s1, s2}, b = {s3, s4, s5, aux}
             const int dir = b.w & 15, k1 = (b.w >> 4) & 15, k2 = b.w >> 8;
-            double v;
+            R v;
             if (a.x == 0) {
                 v = sel3(dir, PA) * sm[a.z] + sel3(dir, WP) * sm[a.w];
                 if (b.x >= 0) v += k1 * (o2p * sm[b.x] - o2pr * sm[b.y]);
@@ -65,8 +71,8 @@ __device__ __forceinline__ void coop_vrr(const CoopTape& tp, double* sm, const d
     }
 }
 
-__device__ __forceinline__ void coop_hrr(const CoopTape& tp, int h, double* sm, const double AB[3],
-                                         const double CD[3], int lane)
+template <typename R>
+__device__ __forceinline__ void coop_hrr(const CoopTape& tp, int h, R* sm, const R AB[3], const R CD[3], int lane)
 {
     const int* ops = tp.hrr[h];
     const int* lvo = tp.hrr_lv[h];
@@ -75,7 +81,7 @@ __device__ __forceinline__ void coop_hrr(const CoopTape& tp, int h, double* sm, 
         for (int o = __ldg(lvo + lv) + lane; o < hi; o += 32) {
             const int4 a = __ldg((const int4*)(ops + 8 * o));
             const int dir = __ldg(ops + 8 * o + 7);
-            const double c = a.x == 3 ? sel3(dir, AB) : sel3(dir, CD);
+            const R c = a.x == 3 ? sel3(dir, AB) : sel3(dir, CD);
             sm[a.y] = sm[a.z] + c * sm[a.w];
         }
         __syncwarp();
@@ -83,15 +89,16 @@ __device__ __forceinline__ void coop_hrr(const CoopTape& tp, int h, double* sm, 
 }
 
 // geometry + Boys of primitive quartet k of (ab|cd) into g (lane-private slot)
-__device__ __forceinline__ void coop_prim(const Pairs& P, int ab, int cd, int k, int npp_ab, const double A[3],
-                                          const double C[3], int L, const double* __restrict__ boys, double* g)
+template <typename R>
+__device__ __forceinline__ void coop_prim(const Pairs& P, int ab, int cd, int k, int npp_ab, int L,
+                                          const R* __restrict__ boys, R* g)
 {
     const int i = k % npp_ab, j = k / npp_ab;
-    double bra[PP_NF], ket[PP_NF];
+    R bra[PP_NF], ket[PP_NF];
     load_ppn(P, ab, i, bra, PP_NF);
     load_ppn(P, cd, j, ket, PP_NF);
-    PrimQuartet q;
-    prim_quartet(bra, ket, q);
+    PrimQ<R> q;
+    prim_quartet<R>(bra, ket, q);
     for (int x = 0; x < 3; x++) {
         g[x] = q.PA[x];
         g[3 + x] = q.WP[x];
@@ -103,34 +110,33 @@ __device__ __forceinline__ void coop_prim(const Pairs& P, int ab, int cd, int k,
     g[14] = q.o2q;
     g[15] = q.o2qr;
     g[16] = q.o2pq;
-    g[17] = 2.0 * bra[PP_EA];
-    g[18] = 2.0 * bra[PP_EB];
-    g[19] = 2.0 * ket[PP_EA];
-    double F[BOYS_MMAX + 1];
+    g[17] = R(2) * bra[PP_EA];
+    g[18] = R(2) * bra[PP_EB];
+    g[19] = R(2) * ket[PP_EA];
+    R F[BOYS_MMAX + 1];
     boys_eval_n(L, q.T, boys, q.theta, F);
     for (int m = 0; m <= L; m++) g[COOP_NG0 + m] = F[m];
 }
 
 // contracted accumulators of one quartet: zero, then every primitive quartet
 // through the VRR and the accumulation ops
+template <typename R>
 __device__ __forceinline__ void coop_primitive_loop(const CoopTape& tp, const Pairs& P, int ab, int cd,
-                                                    const double A[3], const double C[3],
-                                                    const double* __restrict__ boys, double* sm, double* geom,
-                                                    int lane)
+                                                    const R* __restrict__ boys, R* sm, R* geom, int lane)
 {
     const int NG = COOP_NG0 + tp.L + 1;
-    for (int i = lane; i < tp.NACC; i += 32) sm[i] = 0.0;
+    for (int i = lane; i < tp.NACC; i += 32) sm[i] = R(0);
     const int nab = P.npp[ab], npq = nab * P.npp[cd];
     for (int base = 0; base < npq; base += 32) {
-        if (base + lane < npq) coop_prim(P, ab, cd, base + lane, nab, A, C, tp.L, boys, geom + lane * NG);
+        if (base + lane < npq) coop_prim<R>(P, ab, cd, base + lane, nab, tp.L, boys, geom + lane * NG);
         __syncwarp();
         const int nb = min(32, npq - base);
         for (int p = 0; p < nb; p++) {
-            const double* g = geom + p * NG;
+            const R* g = geom + p * NG;
             if (lane <= tp.L) sm[tp.F0 + lane] = g[COOP_NG0 + lane];
             __syncwarp();
-            coop_vrr(tp, sm, g, lane);
-            const double w[4] = {1.0, g[17], g[18], g[19]};
+            coop_vrr<R>(tp, sm, g, lane);
+            const R w[4] = {R(1), g[17], g[18], g[19]};
             for (int o = lane; o < tp.naccop; o += 32) {
                 const int4 a = __ldg((const int4*)(tp.acc + 4 * o));
                 sm[a.x] += (a.z == 0 ? w[0] : (a.z == 1 ? w[1] : (a.z == 2 ? w[2] : w[3]))) * sm[a.y];
@@ -142,30 +148,31 @@ __device__ __forceinline__ void coop_primitive_loop(const CoopTape& tp, const Pa
 
 // one index of a block between Cartesian (nc) and spherical (ns) d components,
 // lane-parallel: fwd: in[n0][6][n2] -> out[n0][5][n2]; else the transpose
-__device__ __forceinline__ void coop_sph_pass(const double* in, double* out, int n0, int l, int n2, bool fwd,
-                                              int lane)
+template <typename R>
+__device__ __forceinline__ void coop_sph_pass(const R* in, R* out, int n0, int l, int n2, bool fwd, int lane)
 {
+    const R s3 = R(kSqrt3), h = R(0.5), hs3 = R(0.5 * kSqrt3);
     const int nin = l < 2 ? ncart(l) : (fwd ? 6 : 5), nout = l < 2 ? ncart(l) : (fwd ? 5 : 6);
     for (int e = lane; e < n0 * nout * n2; e += 32) {
         const int i0 = e / (nout * n2), f = (e / n2) % nout, i2 = e % n2;
-        const double* s = in + (size_t)i0 * nin * n2 + i2;
-        double v;
+        const R* s = in + (size_t)i0 * nin * n2 + i2;
+        R v;
         if (l < 2) {
             v = s[f * n2];
         } else if (fwd) {
-            const double xx = s[0], xy = s[n2], xz = s[2 * n2], yy = s[3 * n2], yz = s[4 * n2], zz = s[5 * n2];
-            v = f == 0 ? kSqrt3 * xy
-              : f == 1 ? kSqrt3 * yz
-              : f == 2 ? zz - 0.5 * (xx + yy)
-              : f == 3 ? kSqrt3 * xz
-                       : 0.5 * kSqrt3 * (xx - yy);
+            const R xx = s[0], xy = s[n2], xz = s[2 * n2], yy = s[3 * n2], yz = s[4 * n2], zz = s[5 * n2];
+            v = f == 0 ? s3 * xy
+              : f == 1 ? s3 * yz
+              : f == 2 ? zz - h * (xx + yy)
+              : f == 3 ? s3 * xz
+                       : hs3 * (xx - yy);
         } else {
-            const double m2 = s[0], m1 = s[n2], m0 = s[2 * n2], p1 = s[3 * n2], p2 = s[4 * n2];
-            v = f == 0 ? -0.5 * m0 + 0.5 * kSqrt3 * p2
-              : f == 1 ? kSqrt3 * m2
-              : f == 2 ? kSqrt3 * p1
-              : f == 3 ? -0.5 * m0 - 0.5 * kSqrt3 * p2
-              : f == 4 ? kSqrt3 * m1
+            const R m2 = s[0], m1 = s[n2], m0 = s[2 * n2], p1 = s[3 * n2], p2 = s[4 * n2];
+            v = f == 0 ? -h * m0 + hs3 * p2
+              : f == 1 ? s3 * m2
+              : f == 2 ? s3 * p1
+              : f == 3 ? -h * m0 - hs3 * p2
+              : f == 4 ? s3 * m1
                        : m0;
         }
         out[e] = v;
@@ -173,8 +180,8 @@ __device__ __forceinline__ void coop_sph_pass(const double* in, double* out, int
     __syncwarp();
 }
 
-template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void coop_cart_to_sph(double* buf, double* tmp, int lane)
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void coop_cart_to_sph(R* buf, R* tmp, int lane)
 {
     constexpr int cb = ncart(LB), cc = ncart(LC), cd = ncart(LD);
     constexpr int sa = nsph(LA), sb = nsph(LB), sc = nsph(LC);
@@ -184,8 +191,8 @@ __device__ __forceinline__ void coop_cart_to_sph(double* buf, double* tmp, int l
     coop_sph_pass(tmp, buf, sa * sb * sc, LD, 1, true, lane);
 }
 
-template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void coop_sph_to_cart_t(double* buf, double* tmp, int lane)
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void coop_sph_to_cart_t(R* buf, R* tmp, int lane)
 {
     constexpr int ca = ncart(LA), cb = ncart(LB), cc = ncart(LC);
     constexpr int sb = nsph(LB), sc = nsph(LC), sd = nsph(LD);
@@ -195,81 +202,84 @@ __device__ __forceinline__ void coop_sph_to_cart_t(double* buf, double* tmp, int
     coop_sph_pass(tmp, buf, ca * cb * cc, LD, 1, false, lane);
 }
 
-// lane-parallel J/K scatter of a spherical block I (see scatter_jk)
-template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void coop_scatter_jk(const double* I, double f, int fa, int fb, int fc, int fd, int N,
-                                                const double* __restrict__ D, double* G, int lane)
+// lane-parallel J/K scatter of a spherical block I (see scatter_jk): the
+// contraction in R, the accumulation into G' in FP64
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void coop_scatter_jk(const R* I, double f, int fa, int fb, int fc, int fd, int N,
+                                                const R* __restrict__ D, double* G, int lane)
 {
     constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
 #define IDX(a, b, c, d) ((((a) * nb + (b)) * nc + (c)) * nd + (d))
 #define DM(i, j) __ldg(D + (size_t)(i) * N + (j))
     for (int e = lane; e < na * nb; e += 32) {
         const int a = e / nb, b = e % nb;
-        double s = 0.0;
+        R s = R(0);
         for (int c = 0; c < nc; c++)
             for (int d = 0; d < nd; d++) s += DM(fc + c, fd + d) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * s);
+        atomicAdd(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s);
     }
     for (int e = lane; e < nc * nd; e += 32) {
         const int c = e / nd, d = e % nd;
-        double s = 0.0;
+        R s = R(0);
         for (int a = 0; a < na; a++)
             for (int b = 0; b < nb; b++) s += DM(fa + a, fb + b) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * s);
+        atomicAdd(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * (double)s);
     }
     for (int e = lane; e < na * nc; e += 32) {
         const int a = e / nc, c = e % nc;
-        double s = 0.0;
+        R s = R(0);
         for (int b = 0; b < nb; b++)
             for (int d = 0; d < nd; d++) s += DM(fb + b, fd + d) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * s);
+        atomicAdd(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * (double)s);
     }
     for (int e = lane; e < nb * nc; e += 32) {
         const int b = e / nc, c = e % nc;
-        double s = 0.0;
+        R s = R(0);
         for (int a = 0; a < na; a++)
             for (int d = 0; d < nd; d++) s += DM(fa + a, fd + d) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * s);
+        atomicAdd(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * (double)s);
     }
     for (int e = lane; e < na * nd; e += 32) {
         const int a = e / nd, d = e % nd;
-        double s = 0.0;
+        R s = R(0);
         for (int b = 0; b < nb; b++)
             for (int c = 0; c < nc; c++) s += DM(fb + b, fc + c) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * s);
+        atomicAdd(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * (double)s);
     }
     for (int e = lane; e < nb * nd; e += 32) {
         const int b = e / nd, d = e % nd;
-        double s = 0.0;
+        R s = R(0);
         for (int a = 0; a < na; a++)
             for (int c = 0; c < nc; c++) s += DM(fa + a, fc + c) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * s);
+        atomicAdd(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * (double)s);
     }
 #undef IDX
 #undef DM
 }
 
-// shared memory (doubles) of one warp
+// shared memory (elements) of one warp
 __host__ __device__ constexpr int coop_warp_doubles(int NACC, int NWORK, int L, int ncart4)
 {
     return NACC + NWORK + 32 * (COOP_NG0 + L + 1) + 2 * ncart4;
 }
 
-template <int LA, int LB, int LC, int LD>
+// Fock build of the quartets whose density-weighted bound lies in [tau_lo, tau_hi)
+template <int LA, int LB, int LC, int LD, typename Rt>
 __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
-                                                      const double* __restrict__ Dall, double* __restrict__ Gall,
-                                                      const double* __restrict__ boys, double tau,
+                                                      const Rt* __restrict__ Dall, double* __restrict__ Gall,
+                                                      const Rt* __restrict__ boys, double tau_lo, double tau_hi,
                                                       const double* __restrict__ Dsh,
                                                       unsigned long long* __restrict__ cnt, CoopTape tp)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Rt* smem = (Rt*)smem_raw;
     constexpr int NC4 = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
     const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = coop_warp_doubles(tp.NACC, tp.NWORK, tp.L, NC4);
-    double* sm = smem + (size_t)w * per;
-    double* geom = sm + tp.NACC + tp.NWORK;
-    double* cart = geom + 32 * (COOP_NG0 + tp.L + 1);
-    double* tmp = cart + NC4;
+    Rt* sm = smem + (size_t)w * per;
+    Rt* geom = sm + tp.NACC + tp.NWORK;
+    Rt* cart = geom + 32 * (COOP_NG0 + tp.L + 1);
+    Rt* tmp = cart + NC4;
     const Tile t = tiles[blockIdx.x];
     if (!R.active[t.rep]) return;
     const int ab = t.ab, r = t.rep;
@@ -284,7 +294,8 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
         const double dq = fmax(fmax(fmax(shell_bound(R, Dsh, r, sa, sb), shell_bound(R, Dsh, r, sc, sd)),
                                     fmax(shell_bound(R, Dsh, r, sa, sc), shell_bound(R, Dsh, r, sa, sd))),
                                fmax(shell_bound(R, Dsh, r, sb, sc), shell_bound(R, Dsh, r, sb, sd)));
-        if (P.Q[ab] * P.Q[cd] * dq < tau) continue;
+        const double bound = P.Q[ab] * P.Q[cd] * dq;
+        if (bound < tau_lo || bound >= tau_hi) continue;
         if (lane == 0) {
             atomicAdd(cnt, 1ull);
             atomicAdd(cnt + 1, (unsigned long long)(P.npp[ab] * P.npp[cd]));
@@ -294,41 +305,43 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        coop_primitive_loop(tp, P, ab, cd, A, Cc, boys, sm, geom, lane);
-        const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-        const double CD[3] = {Cc[0] - Dd[0], Cc[1] - Dd[1], Cc[2] - Dd[2]};
-        coop_hrr(tp, 0, sm, AB, CD, lane);
+        coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, lane);
+        const Rt AB[3] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2])};
+        const Rt CD[3] = {Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
+        coop_hrr<Rt>(tp, 0, sm, AB, CD, lane);
         for (int e = lane; e < NC4; e += 32) cart[e] = sm[__ldg(tp.out[0] + e)];
         __syncwarp();
-        coop_cart_to_sph<LA, LB, LC, LD>(cart, tmp, lane);
+        coop_cart_to_sph<LA, LB, LC, LD, Rt>(cart, tmp, lane);
         double f = 1.0;
         if (sa == sb) f *= 0.5;
         if (sc == sd) f *= 0.5;
         if (ab == cd) f *= 0.5;
         const int N = R.nbf[r];
         const size_t off = R.moff[r];
-        coop_scatter_jk<LA, LB, LC, LD>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off, Gall + off,
-                                        lane);
+        coop_scatter_jk<LA, LB, LC, LD, Rt>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
+                                            Gall + off, lane);
         __syncwarp();
     }
 }
 
-// gradient: derivative blocks of the six shifted classes contracted with Gamma
-template <int LA, int LB, int LC, int LD>
+// gradient: derivative blocks of the six shifted classes contracted with
+// Gamma, for the quartets whose bound Q_ab Q_cd |Gamma| lies in [tau_lo, tau_hi)
+template <int LA, int LB, int LC, int LD, typename Rt>
 __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
                                                           const double* __restrict__ Dall, double* __restrict__ grad,
-                                                          const double* __restrict__ boys, double tau,
+                                                          const Rt* __restrict__ boys, double tau_lo, double tau_hi,
                                                           const double* __restrict__ Dsh, CoopTape tp)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Rt* smem = (Rt*)smem_raw;
     constexpr int NC4 = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
     constexpr int Ls[4] = {LA, LB, LC, LD};
     const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = coop_warp_doubles(tp.NACC, tp.NWORK, tp.L, NC4);
-    double* sm = smem + (size_t)w * per;
-    double* geom = sm + tp.NACC + tp.NWORK;
-    double* gc = geom + 32 * (COOP_NG0 + tp.L + 1);
-    double* tmp = gc + NC4;
+    Rt* sm = smem + (size_t)w * per;
+    Rt* geom = sm + tp.NACC + tp.NWORK;
+    Rt* gc = geom + 32 * (COOP_NG0 + tp.L + 1);
+    Rt* tmp = gc + NC4;
     const Tile t = tiles[blockIdx.x];
     const int ab = t.ab, r = t.rep;
     const int sa = P.sa[ab], sb = P.sb[ab];
@@ -341,13 +354,14 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
     const double* D = Dall + R.moff[r];
     for (int cd = t.c0 + w; cd < t.c1; cd += W) {
         const int sc = P.sa[cd], sd = P.sb[cd];
-        if (P.Q[ab] * P.Q[cd] * gamma_bound(R, Dsh, r, sa, sb, sc, sd) < tau) continue;
+        const double bound = P.Q[ab] * P.Q[cd] * gamma_bound(R, Dsh, r, sa, sb, sc, sd);
+        if (bound < tau_lo || bound >= tau_hi) continue;
         double Cc[3], Dd[3];
         for (int x = 0; x < 3; x++) {
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        coop_primitive_loop(tp, P, ab, cd, A, Cc, boys, sm, geom, lane);
+        coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, lane);
         // Gamma: spherical, then the transpose transform to Cartesian components
         double f = 1.0;
         if (sa == sb) f *= 0.5;
@@ -361,17 +375,17 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
                 const double dab = D[(size_t)(fa + a) * N + fb + b], dcd = D[(size_t)(fc + c) * N + fd + d];
                 const double dac = D[(size_t)(fa + a) * N + fc + c], dbd = D[(size_t)(fb + b) * N + fd + d];
                 const double dad = D[(size_t)(fa + a) * N + fd + d], dbc = D[(size_t)(fb + b) * N + fc + c];
-                gc[e] = f * (4.0 * dab * dcd - dac * dbd - dad * dbc);
+                gc[e] = Rt(f * (4.0 * dab * dcd - dac * dbd - dad * dbc));
             }
             __syncwarp();
-            coop_sph_to_cart_t<LA, LB, LC, LD>(gc, tmp, lane);
+            coop_sph_to_cart_t<LA, LB, LC, LD, Rt>(gc, tmp, lane);
         }
-        const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-        const double CD[3] = {Cc[0] - Dd[0], Cc[1] - Dd[1], Cc[2] - Dd[2]};
-        double gX[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const Rt AB[3] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2])};
+        const Rt CD[3] = {Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
+        Rt gX[3][3] = {{Rt(0), Rt(0), Rt(0)}, {Rt(0), Rt(0), Rt(0)}, {Rt(0), Rt(0), Rt(0)}};
         // tapes in the order Ap, Bp, Cp, then the lowered ones that exist
         for (int h = 0; h < tp.nhrr; h++) {
-            coop_hrr(tp, h, sm, AB, CD, lane);
+            coop_hrr<Rt>(tp, h, sm, AB, CD, lane);
             const int pos = tp.hpos[h];
             const bool up = tp.hup[h] != 0;
             const int lp = Ls[pos] + (up ? 1 : -1);
@@ -386,15 +400,15 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
                 idx[3] = e % ncart(LD);
                 int ex[3];
                 cart_of(Ls[pos], idx[pos], ex[0], ex[1], ex[2]);
-                const double gm = gc[e];
+                const Rt gm = gc[e];
                 for (int x = 0; x < 3; x++) {
                     int eq[3] = {ex[0], ex[1], ex[2]};
-                    double coef = 1.0;
+                    Rt coef = Rt(1);
                     if (up) {
                         eq[x]++;
                     } else {
                         if (ex[x] == 0) continue;
-                        coef = -ex[x];
+                        coef = Rt(-ex[x]);
                         eq[x]--;
                     }
                     int j[4] = {idx[0], idx[1], idx[2], idx[3]};
@@ -405,9 +419,10 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
             }
             __syncwarp();
         }
+        double gd[3][3];
         for (int p = 0; p < 3; p++)
-            for (int x = 0; x < 3; x++) gX[p][x] = warp_sum_d(gX[p][x]);
-        if (lane == 0) scatter_grad<double>(grad, S, sa, sb, sc, sd, gX[0], gX[1], gX[2]);
+            for (int x = 0; x < 3; x++) gd[p][x] = (double)warp_sum_r<Rt>(gX[p][x]);
+        if (lane == 0) scatter_grad<double>(grad, S, sa, sb, sc, sd, gd[0], gd[1], gd[2]);
         __syncwarp();
     }
 }
