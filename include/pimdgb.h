@@ -218,8 +218,8 @@ int pimd_eigh_noalloc(int nmat, int n, const double* A_dev, double* V_dev, doubl
  * 14 basis functions and 8 shells per atom.
  * Network: 96 features -> 3 hidden layers of 256 (SiLU) -> one linear head
  * per pair type (the same atom H, C or O; the element pairs OO, OC, OH, CC,
- * CH, HH), head width = the block size. BF16 tensor-core GEMMs with FP32
- * accumulation, FP32 master weights, Adam. Everything runs on the device of
+ * CH, HH), head width = the block size. BF16 GEMMs on the 5th-generation
+ * tensor cores (tcgen05) with FP32 accumulation, FP32 master weights, Adam. Everything runs on the device of
  * the current CUDA device at creation.
  */
 typedef struct pimd_guess pimd_guess;
@@ -275,11 +275,11 @@ int pimd_guess_mlp_grad(pimd_guess* g, int n, int type, const float* X, const fl
                         float* params_out, float* grads_out);
 /* pimd_bf16_gemm_dev: the network's GEMM alone, C[M][N] (float, device) =
  *   op(A) op(B) with bf16 device matrices A, B (row-major, leading dimensions
- *   lda, ldb; ta / tb = 1 reads the transpose), FP32 accumulation; impl 0 is the
- *   5th-generation tensor-core (tcgen05, TMEM accumulator) kernel the network
- *   uses, 1 the mma.sync kernel. PIMD_ETIMEOUT if a bounded wait expired. */
+ *   lda, ldb; ta / tb = 1 reads the transpose), FP32 accumulation, on the
+ *   5th-generation tensor cores (tcgen05, accumulator in tensor memory).
+ *   PIMD_ETIMEOUT if a bounded wait expired. */
 int pimd_bf16_gemm_dev(int M, int N, int K, const void* A, int lda, int ta, const void* B, int ldb, int tb, float* C,
-                       int ldc, int impl, void* stream);
+                       int ldc, void* stream);
 
 /* Autotuner (the paper has none: its work distribution is a static MPI
  * split): times the Fock build of the given replicas (SAD density, the

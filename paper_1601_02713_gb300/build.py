@@ -28,6 +28,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills", "-w", "-I" + CSRC, "-I" + GEN, "-I" + INCLUDE]
 HAND_WRITTEN = ["onee.cu", "linalg.cu", "scf.cu", "peaks.cu", "guess.cu"]
+# Units whose straight-line kernels ptxas -O3 allocates with 32 registers and
+# tens of kilobytes of local-memory spills per thread (the FP64 (dd|dp) Fock
+# kernel: 94 KB of spill stores); -O1 keeps 255 registers and spills 3-5x
+# less (measured with -Xptxas -v for every unit at both levels).
+PTXAS_O1 = {"tu_eri_dddp", "tu_eri_ddpp", "tu_eri_dpdp", "tu_grad_ddps", "tu_grad_ddss", "tu_grad_dpds",
+            "tu_grad_dppp", "tu_grad_dpps", "tu_grad_dsds", "tu_grad_dspp", "tu_grad_pppp"}
 
 
 def nvcc_path():
@@ -282,7 +288,8 @@ def _compile(args):
         return src, 0.0, ""
     import time
     t = time.time()
-    cmd = [nvcc_path()] + ARCH + FLAGS + ["-c", src, "-o", obj + ".tmp"]
+    extra = ["-Xptxas", "-O1"] if os.path.basename(src)[:-3] in PTXAS_O1 else []
+    cmd = [nvcc_path()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -308,10 +315,12 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             nm = base.split("_")[-1][:-3]
             kind = "eri" if base.startswith("tu_eri_") else "grad"
             deps.append(os.path.join(GEN, f"{kind}_{nm}.cuh"))
-            tp = os.path.join(GEN, f"grad_tape_{nm}.cuh")
-            if kind == "grad" and os.path.exists(tp):
-                deps.append(tp)
-        work.append((src, os.path.join(OBJ, base + ".o"), _deps_hash(src, deps)))
+            for tp in (os.path.join(GEN, f"grad_tape_{nm}.cuh"), os.path.join(GEN, f"coope_{nm}.cuh"),
+                       os.path.join(GEN, f"coopg_{nm}.cuh")):
+                if os.path.exists(tp):
+                    deps.append(tp)
+        extra = "ptxas-O1" if base[:-3] in PTXAS_O1 else ""
+        work.append((src, os.path.join(OBJ, base + ".o"), _deps_hash(src, deps) + extra))
     if force:
         for _, obj, _ in work:
             if os.path.exists(obj + ".sha1"):

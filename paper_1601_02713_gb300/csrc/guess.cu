@@ -18,8 +18,9 @@
 //   representation of the frame on each atom's shells (s: 1, p: the 3x3
 //   rotation, d: the 5x5 matrix of the real solid harmonics).
 // * Network: 96 -> 256 -> 256 -> 256 (SiLU) -> one linear head per pair type,
-//   head width = block size. GEMMs in BF16 on the tensor cores with FP32
-//   accumulation; FP32 master weights and Adam; training on the device.
+//   head width = block size. GEMMs in BF16 on the 5th-generation tensor cores
+//   (tcgen05, FP32 accumulator in tensor memory); FP32 master weights and Adam;
+//   training on the device.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -332,95 +333,48 @@ __global__ void electron_scale_kernel(const RepMat* rms, int nrep, double* D, co
 }
 
 // ---------------------------------------------------------------- BF16 GEMM
-// C[M x N] (fp32) = op(A) op(B) + beta C with A, B bf16 row-major:
-// op(A)(m,k) = ta ? A[k*lda+m] : A[m*lda+k]; op(B)(k,n) = tb ? B[n*ldb+k] : B[k*ldb+n].
-// 64x64 tile per block of 4 warps (32x32 each), K in steps of 32 through shared
-// memory, mma.sync m16n8k16 (bf16 in, fp32 accumulate).
-constexpr int BM = 64, BN = 64, BK = 32, BKP = BK + 8;
+// C[M x N] (fp32) = op(A) op(B) on the 5th-generation tensor cores (see
+// umma_gemm.cuh); every call of the network has beta = 0. A bounded wait that
+// expires sets the per-device flag g_umma_err, checked after each pass.
+__device__ int g_umma_err;
 
-__global__ void __launch_bounds__(128) bf16_gemm_kernel(int M, int N, int K, const __nv_bfloat16* A, int lda,
-                                                        int ta, const __nv_bfloat16* B, int ldb, int tb, float* C,
-                                                        int ldc, float beta)
+static int* umma_err_ptr()
 {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BKP];  // [m][k]
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BKP];  // [n][k]
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) acc[i][j][k] = 0.f;
-    const __nv_bfloat16 z = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int e = threadIdx.x; e < BM * BK; e += 128) {
-            // consecutive threads read consecutive addresses: along m (n) for a
-            // transposed operand, along k otherwise
-            const int mm = ta ? e % BM : e / BK, kka = ta ? e / BM : e % BK;
-            const int m = m0 + mm, ka = k0 + kka;
-            As[mm][kka] = (m < M && ka < K) ? (ta ? A[(size_t)ka * lda + m] : A[(size_t)m * lda + ka]) : z;
-            const int nn = tb ? e / BK : e % BN, kkb = tb ? e % BK : e / BN;
-            const int n = n0 + nn, kb = k0 + kkb;
-            Bs[nn][kkb] = (n < N && kb < K) ? (tb ? B[(size_t)n * ldb + kb] : B[(size_t)kb * ldb + n]) : z;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int r = wm + i * 16;
-                a[i][0] = *(const uint32_t*)&As[r + g][kk + 2 * t];
-                a[i][1] = *(const uint32_t*)&As[r + g + 8][kk + 2 * t];
-                a[i][2] = *(const uint32_t*)&As[r + g][kk + 8 + 2 * t];
-                a[i][3] = *(const uint32_t*)&As[r + g + 8][kk + 8 + 2 * t];
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int n = wn + j * 8 + g;
-                b[j][0] = *(const uint32_t*)&Bs[n][kk + 2 * t];
-                b[j][1] = *(const uint32_t*)&Bs[n][kk + 8 + 2 * t];
-            }
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                        "{%8,%9}, {%0,%1,%2,%3};\n"
-                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                        : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
-        }
-        __syncthreads();
+    static int* ptr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_umma_err) != cudaSuccess) return nullptr;
+        ptr[dev] = (int*)p;
     }
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int m = m0 + wm + i * 16 + g + 8 * h;
-                if (m >= M) continue;
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const int n = n0 + wn + j * 8 + 2 * t + c;
-                    if (n >= N) continue;
-                    float* dst = C + (size_t)m * ldc + n;
-                    *dst = acc[i][j][2 * h + c] + (beta != 0.f ? beta * *dst : 0.f);
-                }
-            }
+    return ptr[dev];
 }
 
 static void gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, int ta, const __nv_bfloat16* B, int ldb,
                       int tb, float* C, int ldc, float beta, cudaStream_t st)
 {
+    (void)beta;
     if (M <= 0 || N <= 0 || K <= 0) return;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    bf16_gemm_kernel<<<grid, 128, 0, st>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, beta);
+    dim3 grid((N + UMMA_N - 1) / UMMA_N, (M + UMMA_M - 1) / UMMA_M);
+    bf16_gemm_tc_kernel<<<grid, 128, 0, st>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, umma_err_ptr());
+}
+
+// 0, or PIMD_ETIMEOUT (and the flag cleared) if a GEMM's bounded wait expired
+static int umma_status(cudaStream_t st)
+{
+    int* p = umma_err_ptr();
+    if (!p) return PIMD_ECUDA;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, p, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PIMD_ECUDA;
+    if (h) {
+        cudaMemsetAsync(p, 0, sizeof(int), st);
+        return PIMD_ETIMEOUT;
+    }
+    return PIMD_OK;
 }
 
 static inline dim3 ew(long long n)
@@ -882,7 +836,7 @@ int guess_predict_device(pimd_guess* g, int nrep, const int* natom_of, const int
     launch_copy_mats(d_rm, nrep, d_tmp, d_D, d_mask, st);
     // the row set is freed on return: wait for the kernels that read it
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return PIMD_ECUDA;
-    return PIMD_OK;
+    return umma_status(st);
 }
 
 }  // namespace pimd
@@ -911,7 +865,8 @@ static int guess_pass(pimd_guess* g, int update, float lr, double* loss)
         tot += l * (double)d->nrep;
     }
     if (loss) *loss = g->ndata > 0 ? tot / (double)g->ndata : 0.0;
-    return cudaGetLastError() == cudaSuccess ? PIMD_OK : PIMD_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return PIMD_ECUDA;
+    return umma_status(st);
 }
 
 extern "C" int pimd_guess_train(pimd_guess* g, int epochs, double lr, double* loss_history)
@@ -964,6 +919,7 @@ extern "C" int pimd_guess_mlp_grad(pimd_guess* g, int n, int type, const float* 
     guess_forward(g, wk, s, st);
     GK(guess_backward(g, wk, s, st));
     if (cudaDeviceSynchronize() != cudaSuccess) return PIMD_ECUDA;
+    GK(umma_status(st));
     cudaMemcpy(loss, s.d_loss, sizeof(double), cudaMemcpyDeviceToHost);
     if (params_out) cudaMemcpy(params_out, g->W, sizeof(float) * g->nparam, cudaMemcpyDeviceToHost);
     if (grads_out) cudaMemcpy(grads_out, g->G, sizeof(float) * g->nparam, cudaMemcpyDeviceToHost);
@@ -1038,28 +994,15 @@ extern "C" int pimd_guess_pair_data(pimd_guess* g, int natom, const int* Z, cons
     return cudaGetLastError() == cudaSuccess ? PIMD_OK : PIMD_ECUDA;
 }
 
-// BF16 GEMM test hook: impl 0 = the tcgen05 kernel, 1 = the mma.sync kernel
+// BF16 GEMM test hook (the network's tensor-core GEMM alone)
 extern "C" int pimd_bf16_gemm_dev(int M, int N, int K, const void* A, int lda, int ta, const void* B, int ldb, int tb,
-                                  float* C, int ldc, int impl, void* stream)
+                                  float* C, int ldc, void* stream)
 {
-    if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (impl != 0 && impl != 1)) return PIMD_EINVAL;
+    if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return PIMD_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    if (impl == 1) {
-        gemm_bf16(M, N, K, (const __nv_bfloat16*)A, lda, ta, (const __nv_bfloat16*)B, ldb, tb, C, ldc, 0.f, st);
-        return cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess ? PIMD_OK : PIMD_ECUDA;
-    }
-    int* d_err;
-    if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return PIMD_ENOMEM;
-    cudaMemsetAsync(d_err, 0, sizeof(int), st);
-    dim3 grid((N + UMMA_N - 1) / UMMA_N, (M + UMMA_M - 1) / UMMA_M);
-    bf16_gemm_tc_kernel<<<grid, 128, 0, st>>>(M, N, K, (const __nv_bfloat16*)A, lda, ta, (const __nv_bfloat16*)B, ldb,
-                                              tb, C, ldc, d_err);
-    int h_err = 0;
-    const bool fine = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-                      cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess;
-    cudaFree(d_err);
-    if (!fine) return PIMD_ECUDA;
-    return h_err ? PIMD_ETIMEOUT : PIMD_OK;
+    gemm_bf16(M, N, K, (const __nv_bfloat16*)A, lda, ta, (const __nv_bfloat16*)B, ldb, tb, C, ldc, 0.f, st);
+    if (cudaGetLastError() != cudaSuccess) return PIMD_ECUDA;
+    return umma_status(st);
 }
 
 // ---------------------------------------------------------------- save / load

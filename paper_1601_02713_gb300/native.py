@@ -108,7 +108,7 @@ def load(path: str | None = None):
     lib.pimd_sad_atomic_density.argtypes = [_P, _P, ctypes.c_int, _D, ctypes.c_int]
     lib.pimd_autotune.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.POINTER(PimdScfOpts), _I, _D]
     lib.pimd_bf16_gemm_dev.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
-                                       ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P]
+                                       ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P]
     lib.pimd_strerror.argtypes = [ctypes.c_int]
     lib.pimd_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -307,14 +307,13 @@ def pimd_autotune(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | Non
     return w[:21].tolist(), float(ms[0])
 
 
-def pimd_bf16_gemm_dev(A, B, C, ta: bool, tb: bool, impl: int = 0, stream: int = 0) -> int:
+def pimd_bf16_gemm_dev(A, B, C, ta: bool, tb: bool, stream: int = 0) -> int:
     """C = op(A) op(B) for bf16 CUDA tensors A, B (row-major) into the float32
-    CUDA tensor C [M, N]; returns the status code."""
+    CUDA tensor C [M, N] on the tensor cores; returns the status code."""
     M, N = int(C.shape[0]), int(C.shape[1])
     K = int(A.shape[0] if ta else A.shape[1])
     return load().pimd_bf16_gemm_dev(M, N, K, _P(A.data_ptr()), int(A.stride(0)), int(ta), _P(B.data_ptr()),
-                                     int(B.stride(0)), int(tb), _P(C.data_ptr()), int(C.stride(0)), int(impl),
-                                     _P(stream))
+                                     int(B.stride(0)), int(tb), _P(C.data_ptr()), int(C.stride(0)), _P(stream))
 
 
 def pimd_last_stats(ctx: Context) -> dict:

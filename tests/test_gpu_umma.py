@@ -21,12 +21,12 @@ import numpy as np
 import torch
 sys.path.insert(0, sys.argv[1])
 from paper_1601_02713_gb300 import native
-M, N, K, ta, tb, impl = map(int, sys.argv[2:8])
+M, N, K, ta, tb = map(int, sys.argv[2:7])
 g = torch.Generator().manual_seed(M * 7 + N * 13 + K)
 A = (torch.randn((K, M) if ta else (M, K), generator=g) * 0.5).to(torch.bfloat16).cuda()
 B = (torch.randn((N, K) if tb else (K, N), generator=g) * 0.5).to(torch.bfloat16).cuda()
 C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
-rc = native.pimd_bf16_gemm_dev(A, B, C, bool(ta), bool(tb), impl)
+rc = native.pimd_bf16_gemm_dev(A, B, C, bool(ta), bool(tb))
 torch.cuda.synchronize()
 a = A.double().cpu().numpy(); b = B.double().cpu().numpy()
 ref = (a.T if ta else a) @ (b.T if tb else b)
@@ -40,12 +40,11 @@ CASES = [(256, 256, 96, 0, 0), (300, 256, 256, 0, 0), (300, 25, 256, 0, 0), (256
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("impl", [0, 1])
-def test_bf16_gemm(case, impl):
+def test_bf16_gemm(case):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    out = subprocess.run([sys.executable, "-c", CHILD, ROOT, *map(str, case), str(impl)], capture_output=True,
+    out = subprocess.run([sys.executable, "-c", CHILD, ROOT, *map(str, case)], capture_output=True,
                          text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     r = json.loads(out.stdout.strip().splitlines()[-1])
