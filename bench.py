@@ -329,7 +329,7 @@ def main():
 
     # autotuner (not timed): Fock-build tile widths for this workload
     t_tune = time.perf_counter()
-    widths, tune_ms = native.pimd_autotune(ctx, basis, Z, seq[0].stacked()[1], opts)
+    widths, grad_var, tune_ms = native.pimd_autotune(ctx, basis, Z, seq[0].stacked()[1], opts)
     t_tune = time.perf_counter() - t_tune
     ctx.clear_guess()
     for i in range(W):
@@ -408,8 +408,11 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nrep * natom * 3 * 8),
                     "d2h_bytes_per_step": int(nrep * 8 + nrep * natom * 3 * 8)},
             "gpu_launches": launches,
-            "autotune": {"tile_widths": widths, "fock_build_ms": tune_ms, "seconds": t_tune,
-                         "note": "ket-tile width per class pair, picked before the warm-up, not timed"},
+            "autotune": {"fock_kernel": widths, "grad_kernel": grad_var, "fock_build_ms": tune_ms,
+                         "seconds": t_tune,
+                         "note": ("per class pair, picked before the warm-up (not timed): Fock ket-tile width "
+                                  "32/64/128 or 0 = warp-cooperative kernel; gradient 0 = warp-cooperative, "
+                                  "1 = straight-line")},
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, thr, sample, secs = oracle_sample(seq[W], kind, statistics.mean(iters), args.cpu_sample_quartets,

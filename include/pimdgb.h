@@ -282,13 +282,16 @@ int pimd_bf16_gemm_dev(int M, int N, int K, const void* A, int lda, int ta, cons
                        int ldc, void* stream);
 
 /* Autotuner (the paper has none: its work distribution is a static MPI
- * split): times the Fock build of the given replicas (SAD density, the
- * options' thresholds) once per candidate ket-tile width (32, 64, 128 quartets
- * per thread block) and keeps, per quartet class pair, the fastest in the
- * context; later calls on the context build their tiles with those widths.
- * widths[n] (n = number of class pairs, 21 for s/p/d; may be NULL) receives
- * the choice and ms_best (may be NULL) the summed time of the chosen widths.
- * Elements up to Z = 10 (it uses the SAD density). */
+ * split): per quartet class pair, times the Fock build of the given replicas
+ * (SAD density, the options' thresholds) with every generated kernel variant
+ * (straight-line kernel with ket tiles of 32, 64 or 128 quartets per block;
+ * warp-cooperative tape kernel) and then the gradient with each of its
+ * variants, and keeps the fastest in the context; later calls on the context
+ * use them. widths[64] (may be NULL): widths[cp] = the Fock choice (32, 64,
+ * 128, or 0 for the cooperative kernel), widths[32 + cp] = the gradient choice
+ * (0 cooperative, 1 straight-line), cp < 21 for s/p/d. ms_best (may be NULL):
+ * the summed Fock-build time of the chosen variants. Elements up to Z = 10
+ * (it uses the SAD density). */
 int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords, const pimd_basis* basis,
                   const pimd_scf_opts* opts, int* widths, double* ms_best);
 

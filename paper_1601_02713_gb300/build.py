@@ -118,6 +118,8 @@ def generate_sources():
     stats = g.generate(GEN)
     heavy = {s[0]: s[6] for s in stats}
     coop_e = {s[0]: s[7] for s in stats}
+    coop_g = {s[0]: s[8] for s in stats}
+    straight_e = {s[0]: s[9] for s in stats}
     classes = g.classes()
     names = [g.cls_name(c) for c in classes]
     tus = []
@@ -130,34 +132,33 @@ def generate_sources():
         e.append("namespace pimd {")
         if coop_e[nm]:
             e += _coop_upload_code(nm, False, g)
-            e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                  "                     const double* D, const float* Df, double* G, const double* boys,",
-                  "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
-                  "                     unsigned long long* cnt, int, cudaStream_t st)",
-                  "{",
-                  "    if (ntiles <= 0) return;",
-                  "    CoopTape t; int W, Wf; size_t bytes, bytesf;",
-                  f"    coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
-                  "    const double split = fp32_tau > tau ? fp32_tau : tau;",
-                  f"    jk_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles, D,",
-                  "        G, boys, split, 1e300, Dsh, cnt, t);",
+        # bs > 0: straight-line kernel with bs threads per block; bs == 0: the
+        # warp-cooperative tape kernel
+        e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
+              "                     const double* D, const float* Df, double* G, const double* boys,",
+              "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
+              "                     unsigned long long* cnt, int bs, cudaStream_t st)",
+              "{",
+              "    if (ntiles <= 0) return;",
+              "    const double split = fp32_tau > tau ? fp32_tau : tau;"]
+        if coop_e[nm]:
+            e += [f"    if (bs == 0{'' if straight_e[nm] else ' || true'}) {{",
+                  "        CoopTape t; int W, Wf; size_t bytes, bytesf;",
+                  f"        coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
+                  f"        jk_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles,",
+                  "            D, G, boys, split, 1e300, Dsh, cnt, t);",
+                  "        if (fp32_tau > tau)",
+                  f"            jk_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S, R,",
+                  "                tiles, Df, G, boysf, tau, fp32_tau, Dsh, cnt + 2, t);",
+                  "        return;",
+                  "    }"]
+        if straight_e[nm]:
+            e += ["    const int b = bs > 0 ? bs : 128;",
+                  f"    jk_kernel<Cls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt);",
                   "    if (fp32_tau > tau)",
-                  f"        jk_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S, R, tiles,",
-                  "            Df, G, boysf, tau, fp32_tau, Dsh, cnt + 2, t);",
-                  "}"]
-        else:
-            e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                  "                     const double* D, const float* Df, double* G, const double* boys,",
-                  "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
-                  "                     unsigned long long* cnt, int bs, cudaStream_t st)",
-                  "{",
-                  "    if (ntiles <= 0) return;",
-                  "    const double split = fp32_tau > tau ? fp32_tau : tau;",
-                  f"    jk_kernel<Cls_{nm}, double><<<ntiles, bs, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt);",
-                  "    if (fp32_tau > tau)",
-                  f"        jk_kernel<Cls_{nm}, float><<<ntiles, bs, 0, st>>>(P, S, R, tiles, Df, G, boysf, tau, fp32_tau, Dsh,",
-                  "                                                        cnt + 2);",
-                  "}"]
+                  f"        jk_kernel<Cls_{nm}, float><<<ntiles, b, 0, st>>>(P, S, R, tiles, Df, G, boysf, tau, fp32_tau, Dsh,",
+                  "                                                       cnt + 2);"]
+        e.append("}")
         if same:
             e += [f"void launch_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
                   "                          const double* boys, double* Q, cudaStream_t st)",
@@ -169,38 +170,40 @@ def generate_sources():
         _write(p, "\n".join(e))
         tus.append(p)
         gl = ['#include "coop_kernels.cuh"', '#include "internal.h"', f'#include "grad_{nm}.cuh"']
-        if heavy[nm]:
+        if coop_g[nm]:
             gl.append(f'#include "coopg_{nm}.cuh"')
         gl.append("namespace pimd {")
-        if not heavy[nm]:
-            gl += [f"void grad2e_upload_{nm}() {{}}",
-                   f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                   "                        const double* D, double* grad, const double* boys, const float* boysf,",
-                   "                        double tau, double fp32_tau, const double* Dsh, cudaStream_t st)",
-                   "{",
-                   "    if (ntiles <= 0) return;",
-                   "    const double split = fp32_tau > tau ? fp32_tau : tau;",
-                   f"    grad2e_kernel<GCls_{nm}, double><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boys, split, 1e300, Dsh);",
-                   "    if (fp32_tau > tau)",
-                   f"        grad2e_kernel<GCls_{nm}, float><<<ntiles, 128, 0, st>>>(P, S, R, tiles, D, grad, boysf, tau, fp32_tau, Dsh);",
-                   "}"]
-        else:
+        if coop_g[nm]:
             gl += _coop_upload_code(nm, True, g)
-            gl += [f"void grad2e_upload_{nm}() {{ CoopTape t; int W, Wf; size_t b, bf; coop_tape_{nm}(t, W, b, Wf, bf); }}",
-                   f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
-                   "                        const double* D, double* grad, const double* boys, const float* boysf,",
-                   "                        double tau, double fp32_tau, const double* Dsh, cudaStream_t st)",
-                   "{",
-                   "    if (ntiles <= 0) return;",
-                   "    CoopTape t; int W, Wf; size_t bytes, bytesf;",
-                   f"    coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
-                   "    const double split = fp32_tau > tau ? fp32_tau : tau;",
-                   f"    grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles,",
-                   "        D, grad, boys, split, 1e300, Dsh, t);",
+            gl.append(f"void grad2e_upload_{nm}() {{ CoopTape t; int W, Wf; size_t b, bf; coop_tape_{nm}(t, W, b, Wf, bf); }}")
+        else:
+            gl.append(f"void grad2e_upload_{nm}() {{}}")
+        # variant 0: warp-cooperative tape kernel, 1: straight-line kernel with bs threads
+        gl += [f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
+               "                        const double* D, double* grad, const double* boys, const float* boysf,",
+               "                        double tau, double fp32_tau, const double* Dsh, int variant, int bs,",
+               "                        cudaStream_t st)",
+               "{",
+               "    if (ntiles <= 0) return;",
+               "    const double split = fp32_tau > tau ? fp32_tau : tau;"]
+        if coop_g[nm]:
+            gl += [f"    if (variant == 0{' || true' if heavy[nm] else ''}) {{",
+                   "        CoopTape t; int W, Wf; size_t bytes, bytesf;",
+                   f"        coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
+                   f"        grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R,",
+                   "            tiles, D, grad, boys, split, 1e300, Dsh, t);",
+                   "        if (fp32_tau > tau)",
+                   f"            grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S,",
+                   "                R, tiles, D, grad, boysf, tau, fp32_tau, Dsh, t);",
+                   "        return;",
+                   "    }"]
+        if not heavy[nm]:
+            gl += ["    const int b = bs > 0 ? bs : 128;",
+                   f"    grad2e_kernel<GCls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boys, split, 1e300, Dsh);",
                    "    if (fp32_tau > tau)",
-                   f"        grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S, R,",
-                   "            tiles, D, grad, boysf, tau, fp32_tau, Dsh, t);",
-                   "}"]
+                   f"        grad2e_kernel<GCls_{nm}, float><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boysf, tau, fp32_tau,",
+                   "                                                           Dsh);"]
+        gl.append("}")
         gl.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_grad_{nm}.cu")
         _write(p, "\n".join(gl))
@@ -211,7 +214,7 @@ def generate_sources():
               "const double*, const float*, double, double, const double*, unsigned long long*, int, cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-             "const float*, double, double, const double*, cudaStream_t")
+             "const float*, double, double, const double*, int, int, cudaStream_t")
     for c, nm in zip(classes, names):
         d.append(f"void launch_jk_{nm}({sig_jk});")
         if (c[0], c[1]) == (c[2], c[3]):
@@ -241,11 +244,13 @@ def generate_sources():
              "const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau, "
              "double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, cudaStream_t st)")
     d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, bs, st); }")
-    d.append("bool class_pair_coop(int cp)")
-    d.append("{")
-    d.append("    static const bool t[] = {" + ", ".join("true" if coop_e[nm] else "false" for nm in names) + "};")
-    d.append("    return t[cp];")
-    d.append("}")
+    for fn, tab in (("class_pair_coop", coop_e), ("class_pair_straight", straight_e), ("grad_pair_coop", coop_g),
+                    ("grad_pair_straight", {nm: not heavy[nm] for nm in names})):
+        d.append(f"bool {fn}(int cp)")
+        d.append("{")
+        d.append("    static const bool t[] = {" + ", ".join("true" if tab[nm] else "false" for nm in names) + "};")
+        d.append("    return t[cp];")
+        d.append("}")
     same = [nm for c, nm in zip(classes, names) if (c[0], c[1]) == (c[2], c[3])]
     d.append(f"typedef void (*SwFn)({sig_sw});")
     d.append("static const SwFn sw_tab[] = {" + ", ".join(f"launch_schwarz_{nm}" for nm in same) + "};")
@@ -257,8 +262,8 @@ def generate_sources():
 
     d.append("void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, double* grad, const double* boys, const float* boysf, double tau, double fp32_tau, "
-             "const double* Dsh, cudaStream_t st)")
-    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, st); }")
+             "const double* Dsh, int variant, int bs, cudaStream_t st)")
+    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, variant, bs, st); }")
     d.append("void grad2e_tapes_upload() {")
     for nm in names:
         d.append(f"    grad2e_upload_{nm}();")

@@ -454,8 +454,12 @@ HRR_NAMES = ["Ap", "Bp", "Cp", "Am", "Bm", "Cm"]
 #   kind 0/1: bra/ket VRR (aux = dir | k1 << 4 | k2 << 8), kind 3/4: bra/ket HRR
 #   (aux = dir); accumulation op = 4 ints {dst, src, weight, 0}.
 # ---------------------------------------------------------------------------
-COOP_ENERGY_MIN_VRR = 2000
-COOP_GRAD_MIN_VRR = HEAVY_GRAD_VRR_LINES
+# a class gets a cooperative tape above these VRR sizes (lines); its
+# straight-line kernel is generated up to the MAX sizes; where both exist the
+# autotuner picks one per class
+COOP_ENERGY_MIN_VRR = 250
+STRAIGHT_ENERGY_MAX_VRR = 2000
+COOP_GRAD_MIN_VRR = 400
 
 
 def _sort_levels(ops, base_level):
@@ -645,6 +649,7 @@ def generate(outdir):
         parts.append("};\n")
         write_if_changed(os.path.join(outdir, f"eri_{nm}.cuh"), "".join(parts))
         coop_e = nl > COOP_ENERGY_MIN_VRR
+        straight_e = nl <= STRAIGHT_ENERGY_MAX_VRR
         if coop_e:
             hdr, _ = coop_header(nm, False, gen_coop(c, False))
             write_if_changed(os.path.join(outdir, f"coope_{nm}.cuh"), hdr)
@@ -666,10 +671,11 @@ def generate(outdir):
                 gparts.append(h)
         gparts.append("};\n")
         write_if_changed(os.path.join(outdir, f"grad_{nm}.cuh"), "".join(gparts))
-        if heavy:
+        coop_g = gnl > COOP_GRAD_MIN_VRR
+        if coop_g:
             hdr, _ = coop_header(nm, True, gen_coop(c, True))
             write_if_changed(os.path.join(outdir, f"coopg_{nm}.cuh"), hdr)
-        stats.append((nm, nl, nfl, nh, gnl, gnfl, heavy, coop_e))
+        stats.append((nm, nl, nfl, nh, gnl, gnfl, heavy, coop_e, coop_g, straight_e))
     return stats
 
 

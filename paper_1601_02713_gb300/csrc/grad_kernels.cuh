@@ -134,7 +134,7 @@ __device__ __forceinline__ double gamma_bound(const Reps& R, const double* Dsh, 
 
 // Straight-line gradient kernel (generated VRR/HRR) in precision R for the
 // quartets whose bound Q_ab Q_cd |Gamma| lies in [tau_lo, tau_hi).
-// blockDim.x == 128.
+// blockDim.x >= the tile's ket width.
 template <class G, typename R>
 __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp, const Tile* __restrict__ tiles,
                                                      const double* __restrict__ Dall, double* __restrict__ grad,
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
     __shared__ R sbra[PP_NF][PIMD_MAXPP];
     const Tile t = tiles[blockIdx.x];
     const int ab = t.ab;
-    if (threadIdx.x < PP_NF * PIMD_MAXPP) {
-        const int f = threadIdx.x / PIMD_MAXPP, k = threadIdx.x % PIMD_MAXPP;
+    for (int e = threadIdx.x; e < PP_NF * PIMD_MAXPP; e += blockDim.x) {
+        const int f = e / PIMD_MAXPP, k = e % PIMD_MAXPP;
         sbra[f][k] = pp_base(P, R(0))[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     }
     __syncthreads();

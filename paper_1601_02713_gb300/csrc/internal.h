@@ -53,20 +53,27 @@ long long class_vrr_flops(int cp);
 // Fock build of one class pair: quartets with bound >= max(tau, fp32_tau) in
 // FP64 (D, boys), those in [tau, fp32_tau) in FP32 (Df, boysf); counters
 // cnt[0..1] FP64 quartets / primitive quartets, cnt[2..3] the same in FP32;
-// bs = threads per block = the tiles' ket width (the warp-cooperative
-// kernels of the largest classes ignore it)
+// bs = threads per block = the tiles' ket width for the straight-line
+// kernel, bs = 0 for the warp-cooperative kernel (a class with one variant
+// ignores the choice)
 void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau,
                double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, cudaStream_t st);
-// the class pair's Fock build runs on the warp-cooperative tape kernel
+// kernel variants generated for a class pair: the warp-cooperative tape
+// kernel and the straight-line kernel, for the Fock build and the gradient
 bool class_pair_coop(int cp);
+bool class_pair_straight(int cp);
+bool grad_pair_coop(int cp);
+bool grad_pair_straight(int cp);
 void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n, const double* boys,
                     double* Q, cudaStream_t st);
 // two-electron gradient of class pair cp: quartets with bound Q_ab Q_cd |Gamma|
-// >= max(tau, fp32_tau) in FP64, those in [tau, fp32_tau) in FP32
+// >= max(tau, fp32_tau) in FP64, those in [tau, fp32_tau) in FP32; variant 0
+// the warp-cooperative kernel, 1 the straight-line kernel with bs threads per
+// block (a class with one variant ignores the choice)
 void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                    const double* D, double* grad, const double* boys, const float* boysf, double tau,
-                   double fp32_tau, const double* Dsh, cudaStream_t st);
+                   double fp32_tau, const double* Dsh, int variant, int bs, cudaStream_t st);
 void grad2e_tapes_upload();   // once per device
 void boys_table_upload(double** dev_tab, float** dev_tabf);
 // FP32 copies for the mixed-precision quartets

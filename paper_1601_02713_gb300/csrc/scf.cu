@@ -103,9 +103,12 @@ struct pimd_ctx {
     cudaEvent_t ev[8];
     int nsm = 152;
     pimd_guess* guess_model = nullptr;   // not owned (guess = 2, 3)
-    // ket width of the quartet tiles per class pair (the Fock-build block
-    // size): 128 until pimd_autotune picks one per class pair
+    // per class pair: ket width of the quartet tiles (the straight-line
+    // Fock kernel's block size), 0 = the warp-cooperative Fock kernel; and the
+    // gradient variant (0 warp-cooperative, 1 straight-line). Defaults until
+    // pimd_autotune times the alternatives: 128 / straight where generated.
     int tile_w[64];
+    int grad_var[64];
     // SAD guess: atomic densities per (basis uid, Z), row-major nbf x nbf
     std::map<std::pair<long long, int>, std::vector<double>> sad;
 };
@@ -193,7 +196,11 @@ extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
     }
     pimd_ctx* ctx = new pimd_ctx();
     ctx->device = device;
-    for (int i = 0; i < 64; i++) ctx->tile_w[i] = 128;
+    for (int i = 0; i < 64; i++) {
+        const bool ok = i < n_class_pairs();
+        ctx->tile_w[i] = ok && !class_pair_straight(i) ? 0 : 128;
+        ctx->grad_var[i] = ok && !grad_pair_straight(i) ? 0 : 1;
+    }
     if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete ctx;
         return PIMD_ECUDA;
@@ -612,7 +619,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     for (int X = 0; X < 6; X++)
         for (int Y = 0; Y <= X; Y++) {
             const int cp = class_pair_index(X, Y);
-            const int tw = ctx->tile_w[cp];
+            const int tw = ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128;
             auto& tl = bt.tiles[cp];
             for (int r = 0; r < nrep; r++) {
                 const int b0 = bt.grp0[r * 6 + X], b1 = bt.grp0[r * 6 + X + 1];
@@ -1271,7 +1278,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         for (int cp = 0; cp < n_class_pairs(); cp++) {
             if (bt.tiles[cp].empty()) continue;
             launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_grad, ctx->boys,
-                          ctx->boysf, o->schwarz_tau * 1e-2, o->fp32_tau, bt.Dsh, ctx->stream);
+                          ctx->boysf, o->schwarz_tau * 1e-2, o->fp32_tau, bt.Dsh, ctx->grad_var[cp],
+                          ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, ctx->stream);
             ctx->stats.kernel_launches += o->fp32_tau > 0 ? 2 : 1;
         }
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
@@ -1476,11 +1484,13 @@ extern "C" int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* nato
 // ---------------------------------------------------------------------------
 // testing hooks
 // ---------------------------------------------------------------------------
-// Autotuner: for each class pair, the ket width of the quartet tiles (the
-// Fock-build block size) that builds the Fock matrix of this workload fastest.
-// Candidates 32, 64, 128; each is timed (CUDA events around every class
-// pair's launch, the second of two builds) on a full Fock build of the SAD
-// density of the given replicas with the options' thresholds.
+// Autotuner: per class pair, the Fock-build kernel (straight-line with ket
+// tiles of 32, 64 or 128 quartets per block, or the warp-cooperative tape
+// kernel, where generated) and then the gradient kernel (straight-line or
+// warp-cooperative, where both exist) that run this workload fastest. Each
+// candidate is timed with CUDA events around the class pair's launches, the
+// second of two passes, on the SAD density of the given replicas with the
+// options' thresholds.
 extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords,
                              const pimd_basis* basis, const pimd_scf_opts* opts, int* widths, double* ms_best)
 {
@@ -1497,59 +1507,106 @@ extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
     ENSURE("xyz", (size_t)nrep * natom * 3, d_xyz);
     CK(cudaMemcpyAsync(d_xyz, coords, sizeof(double) * nrep * natom * 3, cudaMemcpyHostToDevice, ctx->stream));
     const int ncp = n_class_pairs();
-    const int cand[3] = {32, 64, 128};
-    std::vector<double> ms((size_t)ncp * 3, 0.0);
+    const int cand[4] = {32, 64, 128, 0};
+    const double inf = 1e300;
+    std::vector<double> ms((size_t)ncp * 4, inf), gms((size_t)ncp * 2, inf);
     std::vector<cudaEvent_t> ev(2 * (size_t)ncp);
     for (auto& e : ev) CK(cudaEventCreate(&e));
     int rc2 = PIMD_OK;
-    for (int ci = 0; ci < 3 && !rc2; ci++) {
-        for (int cp = 0; cp < ncp; cp++) ctx->tile_w[cp] = cand[ci];
-        Batch bt;
-        if ((rc2 = setup_batch(ctx, bt, nrep, nat.data(), Zc.data(), d_xyz, basis, o.schwarz_tau))) break;
-        Mats m;
-        if ((rc2 = alloc_mats(ctx, bt, m, 2))) break;
+    // one batch with the current widths; the density, bounds and (for the
+    // gradient) the SAD density itself serve every candidate
+    auto prepare = [&](Batch& bt, Mats& m, float** Mf) -> int {
+        int r2 = setup_batch(ctx, bt, nrep, nat.data(), Zc.data(), d_xyz, basis, o.schwarz_tau);
+        if (r2) return r2;
+        if ((r2 = alloc_mats(ctx, bt, m, 2))) return r2;
         std::vector<int> active(nrep, 1);
-        if ((rc2 = upload(ctx, "active", active, &m.active))) break;
+        if ((r2 = upload(ctx, "active", active, &m.active))) return r2;
         bt.R.active = m.active;
-        if ((rc2 = sad_place(ctx, basis, bt, m, Zc.data(), active, m.D))) break;
-        float* Mf = nullptr;
-        if (o.fp32_tau > o.schwarz_tau) {
-            if ((rc2 = dev_ensure(ctx, "Mf", (size_t)bt.mtot, &Mf))) break;
-        }
-        for (int pass = 0; pass < 2 && !rc2; pass++) {
-            cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream);
-            launch_shell_bounds(bt.S, bt.R, bt.nrep, bt.maxsh, m.D, bt.Dsh, bt.R.active, ctx->stream);
-            if (Mf) launch_to_float(m.D, Mf, bt.mtot, ctx->stream);
+        if ((r2 = sad_place(ctx, basis, bt, m, Zc.data(), active, m.D))) return r2;
+        *Mf = nullptr;
+        if (o.fp32_tau > o.schwarz_tau && (r2 = dev_ensure(ctx, "Mf", (size_t)bt.mtot, Mf))) return r2;
+        return PIMD_OK;
+    };
+    auto timed = [&](std::vector<double>& out, int stride, int col, const std::vector<int>& use,
+                     auto&& launch) -> int {
+        for (int pass = 0; pass < 2; pass++) {
             for (int cp = 0; cp < ncp; cp++) {
                 cudaEventRecord(ev[2 * cp], ctx->stream);
-                if (!bt.tiles[cp].empty())
-                    launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, Mf, m.G, ctx->boys,
-                              ctx->boysf, o.schwarz_tau, o.fp32_tau, bt.Dsh, bt.cnt + 4 * cp, cand[ci], ctx->stream);
+                if (use[cp]) launch(cp);
                 cudaEventRecord(ev[2 * cp + 1], ctx->stream);
             }
-            if (cudaStreamSynchronize(ctx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-                rc2 = set_err(ctx, PIMD_ECUDA, "autotune: Fock build failed");
-                break;
-            }
+            if (cudaStreamSynchronize(ctx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+                return set_err(ctx, PIMD_ECUDA, "autotune: kernel failed");
             if (pass == 1)
-                for (int cp = 0; cp < ncp; cp++) {
-                    float t = 0.f;
-                    cudaEventElapsedTime(&t, ev[2 * cp], ev[2 * cp + 1]);
-                    ms[(size_t)cp * 3 + ci] = t;
-                }
+                for (int cp = 0; cp < ncp; cp++)
+                    if (use[cp]) {
+                        float t = 0.f;
+                        cudaEventElapsedTime(&t, ev[2 * cp], ev[2 * cp + 1]);
+                        out[(size_t)cp * stride + col] = t;
+                    }
         }
+        return PIMD_OK;
+    };
+    // Fock build: every candidate width (or the cooperative kernel)
+    for (int ci = 0; ci < 4 && !rc2; ci++) {
+        std::vector<int> use(ncp, 0);
+        for (int cp = 0; cp < ncp; cp++) {
+            const bool ok = cand[ci] > 0 ? class_pair_straight(cp) : class_pair_coop(cp);
+            use[cp] = ok;
+            ctx->tile_w[cp] = ok ? cand[ci] : (class_pair_straight(cp) ? 128 : 0);
+        }
+        Batch bt;
+        Mats m;
+        float* Mf;
+        if ((rc2 = prepare(bt, m, &Mf))) break;
+        cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream);
+        launch_shell_bounds(bt.S, bt.R, bt.nrep, bt.maxsh, m.D, bt.Dsh, bt.R.active, ctx->stream);
+        if (Mf) launch_to_float(m.D, Mf, bt.mtot, ctx->stream);
+        rc2 = timed(ms, 4, ci, use, [&](int cp) {
+            if (!bt.tiles[cp].empty())
+                launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, Mf, m.G, ctx->boys,
+                          ctx->boysf, o.schwarz_tau, o.fp32_tau, bt.Dsh, bt.cnt + 4 * cp, cand[ci], ctx->stream);
+        });
     }
-    for (auto& e : ev) cudaEventDestroy(e);
     double best = 0.0;
     for (int cp = 0; cp < ncp; cp++) {
-        int bi = 2;
+        int bi = class_pair_straight(cp) ? 2 : 3;
         if (!rc2)
-            for (int ci = 0; ci < 3; ci++)
-                if (ms[(size_t)cp * 3 + ci] < ms[(size_t)cp * 3 + bi]) bi = ci;
+            for (int ci = 0; ci < 4; ci++)
+                if (ms[(size_t)cp * 4 + ci] < ms[(size_t)cp * 4 + bi]) bi = ci;
         ctx->tile_w[cp] = cand[bi];
-        best += ms[(size_t)cp * 3 + bi];
+        if (ms[(size_t)cp * 4 + bi] < inf) best += ms[(size_t)cp * 4 + bi];
         if (widths) widths[cp] = cand[bi];
     }
+    // gradient: both variants where both exist, on tiles of the chosen widths
+    if (!rc2) {
+        Batch bt;
+        Mats m;
+        float* Mf;
+        rc2 = prepare(bt, m, &Mf);
+        double* d_g = nullptr;
+        if (!rc2) rc2 = dev_ensure(ctx, "tune_grad", (size_t)nrep * natom * 3, &d_g);
+        if (!rc2) {
+            launch_shell_bounds(bt.S, bt.R, nrep, bt.maxsh, m.D, bt.Dsh, nullptr, ctx->stream);
+            for (int v = 0; v < 2 && !rc2; v++) {
+                std::vector<int> use(ncp, 0);
+                for (int cp = 0; cp < ncp; cp++)
+                    use[cp] = (v == 0 ? grad_pair_coop(cp) : grad_pair_straight(cp)) && !bt.tiles[cp].empty();
+                rc2 = timed(gms, 2, v, use, [&](int cp) {
+                    launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_g,
+                                  ctx->boys, ctx->boysf, o.schwarz_tau * 1e-2, o.fp32_tau, bt.Dsh, v,
+                                  ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, ctx->stream);
+                });
+            }
+        }
+        if (!rc2)
+            for (int cp = 0; cp < ncp; cp++) {
+                const double t0 = gms[(size_t)cp * 2], t1 = gms[(size_t)cp * 2 + 1];
+                if (t0 < inf || t1 < inf) ctx->grad_var[cp] = t0 < t1 ? 0 : 1;
+                if (widths) widths[32 + cp] = ctx->grad_var[cp];
+            }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
     if (ms_best) *ms_best = best;
     return rc2;
 }

@@ -295,8 +295,9 @@ def pimd_sad_atomic_density(ctx: Context, basis: Basis, Z: int):
 
 
 def pimd_autotune(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | None = None):
-    """Pick the Fock-build tile width per class pair for this workload;
-    returns (widths [21], ms of one build with them)."""
+    """Pick the Fock-build kernel (tile width 32/64/128, or 0 = cooperative)
+    and the gradient kernel (0 cooperative, 1 straight-line) per class pair
+    for this workload; returns (fock [21], grad [21], ms of one build)."""
     Z = np.ascontiguousarray(Z, np.int32)
     X = np.ascontiguousarray(coords, np.float64)
     opts = opts or scf_opts()
@@ -304,7 +305,7 @@ def pimd_autotune(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | Non
     ms = np.zeros(1)
     _check(load().pimd_autotune(ctx.handle, X.shape[0], X.shape[1], _ip(Z), _dp(X), basis.handle,
                                 ctypes.byref(opts), _ip(w), _dp(ms)), "pimd_autotune")
-    return w[:21].tolist(), float(ms[0])
+    return w[:21].tolist(), w[32:53].tolist(), float(ms[0])
 
 
 def pimd_bf16_gemm_dev(A, B, C, ta: bool, tb: bool, stream: int = 0) -> int:

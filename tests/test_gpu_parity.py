@@ -267,8 +267,9 @@ def test_autotune_keeps_results(spd):
     r, _ = inputs.workload("water8_spd_32beads", nrep=2)
     Z, X = r.stacked()
     E0, G0, _, _ = native.pimd_bo_forces(c, B, Z, X)
-    widths, ms = native.pimd_autotune(c, B, Z, X)
-    assert len(widths) == 21 and all(w in (32, 64, 128) for w in widths) and ms > 0
+    widths, gvar, ms = native.pimd_autotune(c, B, Z, X)
+    assert len(widths) == 21 and all(w in (0, 32, 64, 128) for w in widths) and ms > 0
+    assert all(v in (0, 1) for v in gvar)
     c.clear_guess()
     E1, G1, info, _ = native.pimd_bo_forces(c, B, Z, X)
     assert all(i["converged"] for i in info)
