@@ -291,3 +291,31 @@ def test_graph_replay_matches_plain_launches(ctx, spd):
     assert [i["iterations"] for i in i0] == [i["iterations"] for i in i1]
     np.testing.assert_allclose(E1, E0, atol=1e-10, rtol=0)
     np.testing.assert_allclose(G1, G0, atol=1e-9, rtol=0)
+
+
+@pytest.mark.parametrize("fp32_tau", [0.0, 1e-6])
+def test_diels_alder_images_against_stored_oracle(ctx, spd, fp32_tau):
+    """String images of uneven size (config 4): the stored oracle images in
+    one ragged batch with their neighbours (C, H and O; 200-296 functions),
+    energies and gradients against the oracle's values stored by
+    tests/golden/make_golden.py."""
+    import glob
+    import os
+    bas, B = spd
+    files = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "da_images_24_rep*.json")))
+    if not files:
+        pytest.skip("no stored Diels-Alder oracle images")
+    reps, _ = inputs.workload("da_images_24")
+    gold = [_golden(os.path.basename(f)) for f in files]
+    idx = sorted({g["replica"] for g in gold} | {4, 9})
+    sub = inputs.Replicas([reps.Z[i] for i in idx], [reps.coords[i] for i in idx])
+    nat, Zc, Xc = sub.concat()
+    E, G, info, rc = native.string_images_forces(ctx, B, nat, Zc, Xc, native.scf_opts(fp32_tau=fp32_tau))
+    assert rc == 0 and all(i["converged"] for i in info)
+    etol, gtol = (E_TOL, G_TOL) if fp32_tau == 0 else (1e-6, 1e-5)
+    off = np.concatenate([[0], np.cumsum(nat)])
+    for g in gold:
+        k = idx.index(g["replica"])
+        assert np.abs(Xc[off[k]:off[k + 1]] - np.array(g["coords_bohr"])).max() < 1e-12
+        assert abs(E[k] - g["energy"]) < etol, (g["replica"], E[k] - g["energy"])
+        assert np.abs(G[off[k]:off[k + 1]] - np.array(g["gradient"])).max() < gtol
