@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--cpu-sample-deriv", type=int, default=8000)
     ap.add_argument("--fp32-tau", type=float, default=0.0,
                     help="mixed precision: quartets with Q_ab Q_cd max|dD| below this run in FP32 (0: all FP64)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernels (straight-line, 128-quartet tiles) instead of tuning them")
     ap.add_argument("--guess-study", action="store_true",
                     help="instead of the benchmark line: train the learned density guess on the GPU and compare "
                          "SCF iterations and evals/s of the guesses (one JSON line)")
@@ -329,7 +331,8 @@ def main():
 
     # autotuner (not timed): Fock-build tile widths for this workload
     t_tune = time.perf_counter()
-    widths, grad_var, tune_ms = native.pimd_autotune(ctx, basis, Z, seq[0].stacked()[1], opts)
+    widths, grad_var, tune_ms = (None, None, None) if args.no_autotune else \
+        native.pimd_autotune(ctx, basis, Z, seq[0].stacked()[1], opts)
     t_tune = time.perf_counter() - t_tune
     ctx.clear_guess()
     for i in range(W):
