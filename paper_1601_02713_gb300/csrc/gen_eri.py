@@ -456,8 +456,11 @@ HRR_NAMES = ["Ap", "Bp", "Cp", "Am", "Bm", "Cm"]
 # ---------------------------------------------------------------------------
 # a class gets a cooperative tape above these VRR sizes (lines); its
 # straight-line kernel is generated up to the MAX sizes; where both exist the
-# autotuner picks one per class
-COOP_ENERGY_MIN_VRR = 250
+# autotuner picks one per class. For the Fock build the cooperative kernel is
+# kept for (dd|dd) alone: timed on a full build it looked faster for (dp|pp)
+# and (dp|dp) too, but in the SCF, whose builds are mostly incremental, it
+# made the whole Fock build 28% slower.
+COOP_ENERGY_MIN_VRR = 2000
 STRAIGHT_ENERGY_MAX_VRR = 2000
 COOP_GRAD_MIN_VRR = 400
 
