@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--cpu-sample-deriv", type=int, default=8000)
     ap.add_argument("--fp32-tau", type=float, default=0.0,
                     help="mixed precision: quartets with Q_ab Q_cd max|dD| below this run in FP32 (0: all FP64)")
+    ap.add_argument("--ref-iterations", type=float, default=15.3,
+                    help="reference arm: SCF iterations per bead evaluation used to scale the oracle sample")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernels (straight-line, 128-quartet tiles) instead of tuning them")
     ap.add_argument("--guess-study", action="store_true",
@@ -182,7 +184,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     seq, kind = make_steps(args.workload, args.nrep, 1, 0)
-    iters = 12.0
+    # SCF iterations per bead evaluation: the mean the GPU path measures on
+    # this workload (15.3 for (H2O)8 with MO reuse between steps)
+    iters = args.ref_iterations
     vals = []
     n_eri = max(1000, args.cpu_sample_quartets // 4)
     n_der = max(200, args.cpu_sample_deriv // 4)
