@@ -101,3 +101,21 @@ def test_mlp_gradient_vs_finite_differences():
         Lp = GO.mse_loss_and_grads(params[:k] + [(W, bp)] + params[k + 1:], X, Y)[0]
         Lm = GO.mse_loss_and_grads(params[:k] + [(W, bm)] + params[k + 1:], X, Y)[0]
         assert abs((Lp - Lm) / (2 * h) - grads[k][1][1]) < 1e-7
+
+
+def test_frames_of_degenerate_geometries():
+    """Frames stay orthonormal and right-handed when the reference atom lies
+    on the pair axis (a linear molecule) and when there is no third atom."""
+    cases = [np.array([[0.0, 0, 0], [0, 0, 1.8], [0, 0, 3.6]]),   # O-H-H on a line
+             np.array([[0.0, 0, 0], [0, 0, 1.4]]),                # H2
+             np.array([[0.0, 0, 0], [1.8, 0, 0], [3.6, 0, 0]])]   # along x: e_z nearly x
+    for xyz in cases:
+        n = len(xyz)
+        for A in range(n):
+            for B in range(n):
+                U = GO.pair_frame(xyz, A, B)
+                np.testing.assert_allclose(U @ U.T, np.eye(3), atol=1e-12)
+                assert abs(np.linalg.det(U) - 1.0) < 1e-12
+                if A != B:
+                    ez = (xyz[B] - xyz[A]) / np.linalg.norm(xyz[B] - xyz[A])
+                    np.testing.assert_allclose(U[2], ez, atol=1e-12)
