@@ -138,7 +138,8 @@ int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* natom_of_img, c
                              const double* coords_concat_dev, const pimd_basis* basis, const pimd_scf_opts* opts,
                              double* energies_dev, double* gradients_concat_dev, pimd_info* info, void* stream);
 
-/* Drop the cached MOs (guess = 1 then starts from the core Hamiltonian). */
+/* Drop the cached MOs (guesses 1, 3 and 5 then start from their fallback:
+ * the core Hamiltonian, the learned density, SAD). */
 void pimd_ctx_clear_guess(pimd_ctx* ctx);
 
 /* Launch statistics of the last forces call: kernels launched, Fock builds,
@@ -166,7 +167,10 @@ int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
  *   D[nrep][N][N] (device), write G = J - K/2 (device, [nrep][N][N]) with
  *   J_mn = sum D_ls (mn|ls), K_mn = sum D_ls (ml|ns) (Schwarz cutoff
  *   schwarz_tau; quartets below fp32_tau in FP32 when fp32_tau > schwarz_tau).
- * pimd_one_electron: S, T, V matrices of one molecule (host arrays [N][N]). */
+ * pimd_one_electron: S, T, V matrices of one molecule (host arrays [N][N]).
+ * pimd_boys_dev: F_dev[i] = F_m(T_dev[i]) = int_0^1 t^(2m) exp(-T t^2) dt for
+ *   n device values, order 0 <= m <= 12 (the tabulated evaluation of the ERI
+ *   kernels). */
 int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords, const pimd_basis* basis,
                   double schwarz_tau, double fp32_tau, const double* D_dev, double* G_dev);
 int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coords, const pimd_basis* basis,
