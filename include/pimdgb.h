@@ -170,7 +170,7 @@ int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
  * pimd_one_electron: S, T, V matrices of one molecule (host arrays [N][N]).
  * pimd_boys_dev: F_dev[i] = F_m(T_dev[i]) = int_0^1 t^(2m) exp(-T t^2) dt for
  *   n device values, order 0 <= m <= 12 (the tabulated evaluation of the ERI
- *   kernels). */
+ *   kernels); a negative or non-finite T gives NaN. */
 int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords, const pimd_basis* basis,
                   double schwarz_tau, double fp32_tau, const double* D_dev, double* G_dev);
 int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coords, const pimd_basis* basis,

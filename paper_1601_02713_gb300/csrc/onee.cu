@@ -610,8 +610,14 @@ __global__ void boys_eval_kernel(int n, int m, const double* T, double* F, const
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double t = T[i];
+    // the table covers T >= 0 only: a negative or non-finite argument gives NaN
+    if (!(t >= 0.0) || !isfinite(t)) {
+        F[i] = nan("");
+        return;
+    }
     double f[BOYS_MMAX + 1];
-    boys_eval_n(m, T[i], boys, 1.0, f);
+    boys_eval_n(m, t, boys, 1.0, f);
     F[i] = f[m];
 }
 
