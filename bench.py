@@ -123,7 +123,7 @@ class ClockSampler:
 # ---------------------------------------------------------------- inputs
 def make_steps(name, nrep, nsteps, rank):
     reps, kind = inputs.workload(name, nrep=nrep)
-    if rank:
+    if rank and reps.uniform():
         # each rank has its own beads: re-seed the bead displacements
         Zb, Xb = reps.Z[0], reps.coords[0] / inputs.ANGSTROM_TO_BOHR
         reps = inputs.beads(Zb, Xb, len(reps.Z), 10_000 * rank + 17, name)
@@ -311,15 +311,22 @@ def main():
     K, W, E2E = args.steps, args.warmup, args.e2e_steps
     seq, kind = make_steps(args.workload, args.nrep, W + K + E2E, rank)
     nrep = len(seq[0].Z)
-    Z, _ = seq[0].stacked()
-    natom = len(Z)
+    # beads of one molecule (pimd_bo_forces) or string images of different
+    # sizes (string_images_forces, one ragged batch)
+    ragged = not seq[0].uniform()
+    if ragged:
+        nat, Z, _ = seq[0].concat()
+        natom = int(nat.sum())
+    else:
+        Z, _ = seq[0].stacked()
+        natom = len(Z)
     ctx = native.Context(local)
     basis = native.Basis(inputs.basis_set(kind))
     opts = native.scf_opts(guess=1, fp32_tau=args.fp32_tau)
     dev = torch.device("cuda", local)
-    X = [torch.tensor(s.stacked()[1], dtype=torch.float64, device=dev) for s in seq]
+    X = [torch.tensor(s.concat()[2] if ragged else s.stacked()[1], dtype=torch.float64, device=dev) for s in seq]
     E = torch.empty(nrep, dtype=torch.float64, device=dev)
-    G = torch.empty(nrep, natom, 3, dtype=torch.float64, device=dev)
+    G = torch.empty((natom, 3) if ragged else (nrep, natom, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (126 MB)
     stream = torch.cuda.current_stream(dev)
 
@@ -328,14 +335,19 @@ def main():
             dist.barrier()
 
     def step(i):
-        infos, rc = native.pimd_bo_forces_dev(ctx, basis, Z, X[i], E, G, opts, stream=stream.cuda_stream)
+        if ragged:
+            infos, rc = native.string_images_forces_dev(ctx, basis, nat, Z, X[i], E, G, opts,
+                                                        stream=stream.cuda_stream)
+        else:
+            infos, rc = native.pimd_bo_forces_dev(ctx, basis, Z, X[i], E, G, opts, stream=stream.cuda_stream)
         if rc != 0:
-            raise RuntimeError(f"pimd_bo_forces_dev returned {rc}")
+            raise RuntimeError(f"forces call returned {rc}")
         return infos
 
-    # autotuner (not timed): Fock-build tile widths for this workload
+    # autotuner (not timed): kernel variants for this workload (replicas of
+    # one molecule; a ragged batch keeps the defaults)
     t_tune = time.perf_counter()
-    widths, grad_var, tune_ms = (None, None, None) if args.no_autotune else \
+    widths, grad_var, tune_ms = (None, None, None) if (args.no_autotune or ragged) else \
         native.pimd_autotune(ctx, basis, Z, seq[0].stacked()[1], opts)
     t_tune = time.perf_counter() - t_tune
     ctx.clear_guess()
@@ -369,14 +381,17 @@ def main():
     # the step inputs in pinned host memory (the H2D copy is part of the call)
     Xh = []
     for i in range(W + K, W + K + E2E):
-        x = seq[i].stacked()[1]
+        x = seq[i].concat()[2] if ragged else seq[i].stacked()[1]
         xp = torch.empty(x.shape, dtype=torch.float64, pin_memory=torch.cuda.is_available()).numpy()
         xp[...] = x
         Xh.append(xp)
     barrier()
     t0 = time.perf_counter()
     for x in Xh:
-        Eh, Gh, info_h, rc = native.pimd_bo_forces(ctx, basis, Z, x, opts)
+        if ragged:
+            Eh, Gh, info_h, rc = native.string_images_forces(ctx, basis, nat, Z, x, opts)
+        else:
+            Eh, Gh, info_h, rc = native.pimd_bo_forces(ctx, basis, Z, x, opts)
         assert rc == 0
     t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_value = job_throughput(nrep, world, E2E, t_e2e)
@@ -391,11 +406,21 @@ def main():
     geri = eris / (fock_ms * 1e-3) / 1e9
     launches = int(sum(s["kernel_launches"] for s in stats))
 
+    Bq = native.Basis(inputs.basis_set(kind))
+    if ragged:
+        nbfs = [Bq.nbf(z) for z in seq[0].Z]
+        basis_txt = f"{kind} (even-tempered, {min(nbfs)}-{max(nbfs)} functions per image)"
+        coord_bytes = natom * 3 * 8
+    else:
+        basis_txt = f"{kind} (even-tempered, {Bq.nbf(Z)} functions)"
+        coord_bytes = nrep * natom * 3 * 8
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.fp32_tau == 0 else "f64+f32", "data": "synthetic",
-            "config": {"workload": args.workload, "beads_per_rank": nrep, "atoms": natom,
-                       "basis": f"{kind} (even-tempered, {native.Basis(inputs.basis_set(kind)).nbf(Z)} functions)",
+            "config": {"workload": args.workload, "beads_per_rank": nrep,
+                       "atoms": natom if not ragged else f"{min(len(z) for z in seq[0].Z)}-"
+                                                         f"{max(len(z) for z in seq[0].Z)} per image",
+                       "basis": basis_txt,
                        "scf": "|dE|<1e-10, max|FDS-SDF|<1e-8, DIIS(8), MO reuse between steps",
                        "schwarz_tau": 1e-12, "fp32_tau": args.fp32_tau,
                        "l2": "flushed before every timed step (512 MB write)",
@@ -418,8 +443,8 @@ def main():
                                   "pipe (mixed mode); their sum is the share of the two pipes' peak the build uses"),
                          "flops_per_launch": flops / max(builds, 1), "ms_per_launch": fock_ms / max(builds, 1),
                          "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (FMA chain measured 1.255)"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nrep * natom * 3 * 8),
-                    "d2h_bytes_per_step": int(nrep * 8 + nrep * natom * 3 * 8)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(coord_bytes),
+                    "d2h_bytes_per_step": int(nrep * 8 + coord_bytes)},
             "gpu_launches": launches,
             "autotune": {"fock_kernel": widths, "grad_kernel": grad_var, "fock_build_ms": tune_ms,
                          "seconds": t_tune,
