@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(128) bf16_gemm_tc_kernel(int M, int N, int K, 
         ok = __syncthreads_and(ok ? 1 : 0) != 0;
     }
     if (!ok) {
-        if (threadIdx.x == 0) atomicExch(err, 1);
+        if (threadIdx.x == 0 && err) atomicExch(err, 1);
         umma_wait(bar_a, phase ^ 1u);
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
