@@ -87,3 +87,31 @@ def test_generated_sources_are_deterministic():
         g.generate(d2)
         for f in sorted(os.listdir(d1)):
             assert open(os.path.join(d1, f)).read() == open(os.path.join(d2, f)).read(), f
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the offsets and sizes the C
+    compiler gives the header's structs (a header/binding drift would
+    silently misread options or statistics)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pimd_scf_opts": native.PimdScfOpts, "pimd_info": native.PimdInfo, "pimd_stats": native.PimdStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pimdgb.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
