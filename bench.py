@@ -404,6 +404,7 @@ def main():
     eris = sum(s["eris_per_build"] * s["fock_builds"] for s in stats)
     achieved = flops / (fock_ms * 1e-3) / 1e12
     geri = eris / (fock_ms * 1e-3) / 1e9
+    eris32 = sum(s.get("eris32_per_build", 0.0) * s["fock_builds"] for s in stats)
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     Bq = native.Basis(inputs.basis_set(kind))
@@ -426,6 +427,9 @@ def main():
                        "l2": "flushed before every timed step (512 MB write)",
                        "parallelism": f"replicas{world}"},
             "geri_per_s": geri,
+            "geri_per_s_split": {"fp64": (eris - eris32) / (fock_ms * 1e-3) / 1e9,
+                                 "fp32": eris32 / (fock_ms * 1e-3) / 1e9,
+                                 "note": "unique contracted ERIs of each path over the whole Fock-build time"},
             "fp32_quartet_fraction": (sum(s["quartets_fp32"] for s in stats)
                                       / max(1, sum(s["quartets_fp32"] + s["quartets_fp64"] for s in stats))),
             "fock_builds_per_step": builds / K,

@@ -159,6 +159,7 @@ typedef struct {
     double eri_flops32_per_build;  /* the same operations count for the FP32 quartets (mixed mode) */
     long long quartets_fp64;     /* executed shell quartets of all Fock builds of the call, FP64 */
     long long quartets_fp32;     /* ... and FP32 (fp32_tau > 0) */
+    double eris32_per_build;     /* the part of eris_per_build evaluated in FP32 */
 } pimd_stats;
 int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
 

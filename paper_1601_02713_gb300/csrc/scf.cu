@@ -1320,7 +1320,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         // executed work of all Fock builds of the call, from the device counters
         std::vector<unsigned long long> cnt(4 * 64);
         CK(cudaMemcpy(cnt.data(), bt.cnt, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
-        double fl = 0.0, er = 0.0, fl32 = 0.0;
+        double fl = 0.0, er = 0.0, fl32 = 0.0, er32 = 0.0;
         long long q64 = 0, q32 = 0;
         for (int cp = 0; cp < n_class_pairs(); cp++) {
             int la, lb, lc, ld;
@@ -1329,6 +1329,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             fl += (double)cnt[4 * cp + 1] * class_vrr_flops(cp);
             fl32 += (double)cnt[4 * cp + 3] * class_vrr_flops(cp);
             er += (double)(cnt[4 * cp] + cnt[4 * cp + 2]) * nfun;
+            er32 += (double)cnt[4 * cp + 2] * nfun;
             q64 += (long long)cnt[4 * cp];
             q32 += (long long)cnt[4 * cp + 2];
         }
@@ -1336,6 +1337,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         ctx->stats.eri_flops_per_build = fl / nb;
         ctx->stats.eri_flops32_per_build = fl32 / nb;
         ctx->stats.eris_per_build = er / nb;
+        ctx->stats.eris32_per_build = er32 / nb;
         ctx->stats.quartets_fp64 = q64;
         ctx->stats.quartets_fp32 = q32;
     }

@@ -34,7 +34,8 @@ class PimdStats(ctypes.Structure):
                 ("ms_fock", ctypes.c_double), ("ms_grad2e", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("nquartets_total", ctypes.c_longlong), ("eri_flops_per_build", ctypes.c_double),
                 ("eris_per_build", ctypes.c_double), ("eri_flops32_per_build", ctypes.c_double),
-                ("quartets_fp64", ctypes.c_longlong), ("quartets_fp32", ctypes.c_longlong)]
+                ("quartets_fp64", ctypes.c_longlong), ("quartets_fp32", ctypes.c_longlong),
+                ("eris32_per_build", ctypes.c_double)]
 
 
 class PimdError(RuntimeError):
