@@ -6,8 +6,9 @@
 // contracted [e0|f0] accumulators, then the generated Head-Gordon-Pople
 // horizontal recursion gives the Cartesian block, which is turned into real
 // spherical d functions and contracted with the density on the fly.
-// A block of 128 threads shares one bra pair (staged in shared memory) and
-// walks 128 ket pairs of the same class, so the code path is uniform across
+// A block shares one bra pair (staged in shared memory) and walks a tile of
+// 32, 64 or 128 ket pairs of the same class (one thread each; the width is
+// chosen per class pair by the autotuner), so the code path is uniform across
 // the block. Every replica of the call is covered by the same launch.
 //
 // Quartets are the canonical ones (a >= b, c >= d, ab >= cd); each is
