@@ -177,6 +177,11 @@ int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double
 int pimd_one_electron(pimd_ctx* ctx, int natom, const int* Z, const double* coords, const pimd_basis* basis,
                       double* S, double* T, double* V);
 int pimd_boys_dev(pimd_ctx* ctx, int n, int m, const double* T_dev, double* F_dev);
+/* pimd_boys_f32_dev: the same function in the FP32 evaluation of the
+ *   mixed-precision quartets (float T_dev[n] -> float F_dev[n], 0 <= m <= 12);
+ *   variant 0 is the compile-time-order form of the straight-line ERI
+ *   kernels, 1 the runtime-order form of the warp-cooperative kernels. */
+int pimd_boys_f32_dev(pimd_ctx* ctx, int n, int m, const float* T_dev, float* F_dev, int variant);
 /* pimd_sad_atomic_density: the atomic density of element Z used by the SAD
  * guess (guess = 4, 5), host array D[n][n], n = functions of Z in the basis. */
 int pimd_sad_atomic_density(pimd_ctx* ctx, const pimd_basis* basis, int Z, double* D, int n);
@@ -189,7 +194,8 @@ int pimd_sad_atomic_density(pimd_ctx* ctx, const pimd_basis* basis, int Z, doubl
  * vector k). One-sided Jacobi on A + sigma I (sigma from the Gershgorin
  * bound), n <= 768. Uses a workspace of the context (allocated on demand).
  * stream: the caller's cudaStream_t or NULL; the call returns after the results
- * are written. */
+ * are written. PIMD_ENOTCONV (results written) if some matrix is still
+ * rotating after 60 sweeps. */
 int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev,
                   void* stream);
 
@@ -202,10 +208,15 @@ int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V
  * matrix descriptors, held by every GPU that loads the library until the
  * process exits. Limits: n <= 768, nmat <= 1024 and nmat * n * n <= 2,097,152, else
  * PIMD_EINVAL. Arguments as for pimd_eigh_dev; no context is needed (the
- * current CUDA device is used). The first call on a device resolves the
- * array addresses on that device; make that first call before any stream
- * capture. All calls share the one workspace: calls that overlap on the GPU
- * (from several host threads or streams) race and give wrong results. */
+ * current CUDA device is used). Unlike pimd_eigh_dev, the call only enqueues
+ * its kernels on `stream` and returns without waiting for them: the results
+ * are in V_dev and evals_dev once the stream reaches that point, and a matrix
+ * that exceeds the solver's sweep limit is not reported (pimd_eigh_dev returns
+ * PIMD_ENOTCONV for it). The first call on a device resolves the array
+ * addresses on that device; make that first call before any stream capture.
+ * All calls share the one workspace, which keeps the last call's contents
+ * (the solver overwrites every element it reads): calls that overlap on the
+ * GPU (from several host threads or streams) race and give wrong results. */
 int pimd_eigh_noalloc(int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev, void* stream);
 
 /* ------------------------------------------------------------------------

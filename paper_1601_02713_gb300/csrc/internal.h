@@ -98,9 +98,10 @@ struct RepMat {       // per replica matrix view
     long long off;    // element offset of the N x N matrices
 };
 // one-sided Jacobi eigensolver of symmetric A (per replica, ascending order):
-// evals[rep][N] (offset rep * ldE), V columns = eigenvectors (row-major N x N at off)
+// evals[rep][N] (offset rep * ldE), V columns = eigenvectors (row-major N x N at off);
+// notconv[rep] (may be NULL) is set to 1 for a matrix still rotating after the sweep limit
 void launch_jacobi(const RepMat* d_rm, int nrep, const double* A, double* V, double* evals, int ldE,
-                   double* work, const int* active, int shift_to_spd, cudaStream_t st);
+                   double* work, const int* active, int shift_to_spd, cudaStream_t st, int* notconv = nullptr);
 
 void launch_fock_assemble(const RepMat* rm, int nrep, const double* h, const double* G, double* F,
                           const int* active, cudaStream_t st);
@@ -125,6 +126,7 @@ void launch_copy_mats(const RepMat* rm, int nrep, const double* src, double* dst
                       cudaStream_t st);
 void launch_identity(const RepMat* rm, int nrep, double* A, const int* mask, cudaStream_t st);
 void launch_boys_eval(int n, int m, const double* T, double* F, const double* boys, cudaStream_t st);
+void launch_boys_eval_f32(int n, int m, const float* T, float* F, const float* boysf, int variant, cudaStream_t st);
 void gather_xyz(const double* atom_xyz, const int* shell_atom, int nshell, double* shell_xyz, cudaStream_t st);
 void add_mats(const RepMat* rm, int nrep, const double* A, const double* B, double* C, cudaStream_t st);
 void diis_set_stride(long long stride);

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "pimdgb.h"
 
 namespace pimd {
 
@@ -94,10 +95,12 @@ __device__ __forceinline__ double warp_sum(double v)
 // PER = column elements held per lane (n <= 32 PER): the kernel is FP64-bound
 // on one SM per matrix, so PER is the smallest instantiated length that fits
 // the batch's largest matrix (padding lanes would be FP64 work on zeros).
+// notconv (may be NULL): notconv[r] = 1 when matrix r is still rotating after
+// JAC_MAXSWEEP sweeps (its eigenpairs are then not converged)
 template <int PER>
 __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __restrict__ rms, const double* A,
                                                              double* V, double* evals, int ldE, double* work,
-                                                             const int* active, int shift_to_spd)
+                                                             const int* active, int shift_to_spd, int* notconv)
 {
     const int r = blockIdx.x;
     if (active && !active[r]) return;
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
     __syncthreads();
     const int M = (n + 1) & ~1;  // even number of players; index n is a dummy when n is odd
     const double tol = 4e-16 * (n > 8 ? n : 8);
+    bool settled = false;
     for (int sweep = 0; sweep < JAC_MAXSWEEP; sweep++) {
         if (threadIdx.x == 0) s_rot = 0;
         __syncthreads();
@@ -191,9 +195,13 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
         }
         if (rotated) s_rot = 1;
         __syncthreads();
-        if (!s_rot) break;
+        if (!s_rot) {
+            settled = true;
+            break;
+        }
         __syncthreads();
     }
+    if (!settled && notconv && threadIdx.x == 0) notconv[r] = 1;
     // eigenvalues (column norms minus the shift), ascending order by rank
     extern __shared__ double s_lam[];
     for (int j = threadIdx.x; j < n; j += JAC_THREADS) {
@@ -217,23 +225,23 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
 
 // one block per matrix; nmax = the largest n of the batch (<= 32 JAC_PER)
 static void jacobi_dispatch(int nmat, int nmax, cudaStream_t st, const RepMat* rm, const double* A, double* V,
-                            double* evals, int ldE, double* work, const int* active, int shift)
+                            double* evals, int ldE, double* work, const int* active, int shift, int* notconv)
 {
     const size_t sm = sizeof(double) * nmax;
     if (nmax <= 32 * 2)
-        jacobi_kernel<2><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+        jacobi_kernel<2><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 4)
-        jacobi_kernel<4><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+        jacobi_kernel<4><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 6)
-        jacobi_kernel<6><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+        jacobi_kernel<6><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 8)
-        jacobi_kernel<8><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+        jacobi_kernel<8><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 12)
-        jacobi_kernel<12><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+        jacobi_kernel<12><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 16)
-        jacobi_kernel<16><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+        jacobi_kernel<16><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
     else
-        jacobi_kernel<JAC_PER><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift);
+        jacobi_kernel<JAC_PER><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
 }
 
 __global__ void fock_assemble_kernel(const RepMat* rms, const double* h, const double* G, double* F,
@@ -568,7 +576,14 @@ static __device__ __align__(256) RepMat g_eigh_desc[PIMD_EIGH_NOALLOC_MAX_MATS];
 // above are host-side stand-ins and must never be passed to a kernel)
 static double* g_eigh_work_ptr[64];
 static RepMat* g_eigh_desc_ptr[64];
-static RepMat g_eigh_desc_host[64][PIMD_EIGH_NOALLOC_MAX_MATS];
+
+// descriptors of nmat consecutive n x n matrices, written on the device (no
+// host staging buffer, so the call only enqueues work on its stream)
+__global__ void eigh_desc_kernel(RepMat* desc, int nmat, int n)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nmat; r += gridDim.x * blockDim.x)
+        desc[r] = RepMat{n, 0, (long long)r * n * n};
+}
 
 void launch_identity(const RepMat* rm, int nrep, double* A, const int* mask, cudaStream_t st)
 {
@@ -588,12 +603,12 @@ void launch_gemm(const GemmDesc* d_desc, int ndesc, int maxM, int maxN, const in
 }
 
 void launch_jacobi(const RepMat* d_rm, int nrep, const double* A, double* V, double* evals, int ldE, double* work,
-                   const int* active, int shift_to_spd, cudaStream_t st)
+                   const int* active, int shift_to_spd, cudaStream_t st, int* notconv)
 {
     // ldE is the largest n of the batch; the kernel holds 32 * JAC_PER column elements per warp
     if (ldE > 32 * JAC_PER) return;
     if (nrep == 0) return;
-    jacobi_dispatch(nrep, ldE, st, d_rm, A, V, evals, ldE, work, active, shift_to_spd);
+    jacobi_dispatch(nrep, ldE, st, d_rm, A, V, evals, ldE, work, active, shift_to_spd, notconv);
 }
 
 static dim3 elem_grid(int nrep) { return dim3(64, nrep); }
@@ -684,29 +699,25 @@ void launch_diis_combine(const RepMat* rm, int nrep, const double* Fh, const dou
 
 int eigh_noalloc(int nmat, int n, const double* A, double* V, double* evals, cudaStream_t st)
 {
-    if (nmat <= 0 || n <= 0 || !A || !V || !evals) return -1;
+    if (nmat <= 0 || n <= 0 || !A || !V || !evals) return PIMD_EINVAL;
     if (nmat > PIMD_EIGH_NOALLOC_MAX_MATS || (long long)nmat * n * n > PIMD_EIGH_NOALLOC_MAX_DOUBLES ||
         n > 32 * JAC_PER)
-        return -1;
+        return PIMD_EINVAL;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -3;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PIMD_ECUDA;
     if (!g_eigh_work_ptr[dev]) {
         // set-up on the first call on this device
         void* w = nullptr;
         void* d = nullptr;
-        if (cudaGetSymbolAddress(&w, g_eigh_work) != cudaSuccess) return -3;
-        if (cudaGetSymbolAddress(&d, g_eigh_desc) != cudaSuccess) return -3;
+        if (cudaGetSymbolAddress(&w, g_eigh_work) != cudaSuccess) return PIMD_ECUDA;
+        if (cudaGetSymbolAddress(&d, g_eigh_desc) != cudaSuccess) return PIMD_ECUDA;
         g_eigh_desc_ptr[dev] = (RepMat*)d;
         g_eigh_work_ptr[dev] = (double*)w;
     }
-    RepMat* hd = g_eigh_desc_host[dev];
-    for (int r = 0; r < nmat; r++) hd[r] = RepMat{n, 0, (long long)r * n * n};
-    if (cudaMemcpyAsync(g_eigh_desc_ptr[dev], hd, sizeof(RepMat) * nmat, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return -3;
-    jacobi_dispatch(nmat, n, st, g_eigh_desc_ptr[dev], A, V, evals, n, g_eigh_work_ptr[dev], nullptr, 1);
-    if (cudaGetLastError() != cudaSuccess) return -3;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
-    return 0;
+    eigh_desc_kernel<<<(nmat + 127) / 128, 128, 0, st>>>(g_eigh_desc_ptr[dev], nmat, n);
+    jacobi_dispatch(nmat, n, st, g_eigh_desc_ptr[dev], A, V, evals, n, g_eigh_work_ptr[dev], nullptr, 1, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return PIMD_ECUDA;
+    return PIMD_OK;
 }
 
 }  // namespace pimd

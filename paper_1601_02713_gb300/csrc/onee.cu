@@ -621,7 +621,58 @@ __global__ void boys_eval_kernel(int n, int m, const double* T, double* F, const
     F[i] = f[m];
 }
 
+// FP32 evaluation of the mixed-precision quartets: variant 0 the
+// compile-time-order form of the straight-line kernels, 1 the runtime-order
+// form of the warp-cooperative kernels
+template <int L>
+__device__ __forceinline__ float boys_f32_fixed(float t, const float* boysf)
+{
+    float f[L + 1];
+    boys_eval<L>(t, boysf, 1.0f, f);
+    return f[L];
+}
+
+__global__ void boys_eval_f32_kernel(int n, int m, const float* T, float* F, const float* boysf, int variant)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float t = T[i];
+    if (!(t >= 0.0f) || !isfinite(t)) {
+        F[i] = nanf("");
+        return;
+    }
+    if (variant == 1) {
+        float f[BOYS_MMAX + 1];
+        boys_eval_n(m, t, boysf, 1.0f, f);
+        F[i] = f[m];
+        return;
+    }
+    float v = 0.0f;
+    switch (m) {
+    case 0: v = boys_f32_fixed<0>(t, boysf); break;
+    case 1: v = boys_f32_fixed<1>(t, boysf); break;
+    case 2: v = boys_f32_fixed<2>(t, boysf); break;
+    case 3: v = boys_f32_fixed<3>(t, boysf); break;
+    case 4: v = boys_f32_fixed<4>(t, boysf); break;
+    case 5: v = boys_f32_fixed<5>(t, boysf); break;
+    case 6: v = boys_f32_fixed<6>(t, boysf); break;
+    case 7: v = boys_f32_fixed<7>(t, boysf); break;
+    case 8: v = boys_f32_fixed<8>(t, boysf); break;
+    case 9: v = boys_f32_fixed<9>(t, boysf); break;
+    case 10: v = boys_f32_fixed<10>(t, boysf); break;
+    case 11: v = boys_f32_fixed<11>(t, boysf); break;
+    default: v = boys_f32_fixed<12>(t, boysf); break;
+    }
+    F[i] = v;
+}
+
 }  // namespace
+
+void launch_boys_eval_f32(int n, int m, const float* T, float* F, const float* boysf, int variant, cudaStream_t st)
+{
+    if (n == 0) return;
+    boys_eval_f32_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, m, T, F, boysf, variant);
+}
 
 void launch_pair_data(const Pairs& P, int* npp, double* pp, const Shells& S, const BasisPrimDev& B,
                       cudaStream_t st)

@@ -670,6 +670,7 @@ struct Mats {
     double *E, *emax, *enn;
     double *Dp, *dD;
     int *slot, *count, *diis_on, *active, *fin, *mode;
+    int* jnc;   // per replica: the eigensolver hit its sweep limit in this call
     RepMat* rm;
     int ldE;
 };
@@ -712,6 +713,8 @@ static int alloc_mats(pimd_ctx* ctx, Batch& bt, Mats& m, int hist)
     ENSURE("count", bt.nrep, m.count);
     ENSURE("diis_on", bt.nrep, m.diis_on);
     ENSURE("fin", bt.nrep, m.fin);
+    ENSURE("jac_nc", bt.nrep, m.jnc);
+    CK(cudaMemsetAsync(m.jnc, 0, sizeof(int) * bt.nrep, ctx->stream));
     m.active = (int*)bt.R.active;
     std::vector<RepMat> rm(bt.nrep);
     for (int r = 0; r < bt.nrep; r++) rm[r] = RepMat{bt.nbf[r], bt.nocc[r], bt.moff[r]};
@@ -780,7 +783,7 @@ static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, co
     gemm(ctx, p.XtFX, mask);   // F' -> Cs
     gemm(ctx, p.QtF, mask);
     gemm(ctx, p.FQ, mask);     // F'' -> M2
-    launch_jacobi(m.rm, bt.nrep, m.M2, m.Cp, m.Ev, m.ldE, m.work, mask, 1, ctx->stream);
+    launch_jacobi(m.rm, bt.nrep, m.M2, m.Cp, m.Ev, m.ldE, m.work, mask, 1, ctx->stream, m.jnc);
     gemm(ctx, p.QU, mask);     // Q U -> M1
     launch_copy_mats(m.rm, bt.nrep, m.M1, m.Cq, mask, ctx->stream);
     gemm(ctx, p.XC, mask);
@@ -1083,7 +1086,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         launch_vnn(bt.At, bt.atom0[nrep], d_ar, m.enn, nullptr, ctx->stream);
     }
     // X = S^{-1/2}
-    launch_jacobi(m.rm, nrep, m.S, m.Cp, m.Ev, m.ldE, m.work, nullptr, 0, ctx->stream);
+    launch_jacobi(m.rm, nrep, m.S, m.Cp, m.Ev, m.ldE, m.work, nullptr, 0, ctx->stream, m.jnc);
     ctx->stats.kernel_launches += 5;
     {
         std::vector<double> ev((size_t)nrep * m.ldE);
@@ -1341,8 +1344,11 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         ctx->stats.quartets_fp64 = q64;
         ctx->stats.quartets_fp32 = q32;
     }
+    std::vector<int> jnc(nrep);
+    CK(cudaMemcpy(jnc.data(), m.jnc, sizeof(int) * nrep, cudaMemcpyDeviceToHost));
     bool allconv = true;
     for (int r = 0; r < nrep; r++) {
+        if (jnc[r]) conv[r] = 0;   // a diagonalisation of the replica did not converge
         if (info) {
             info[r].iterations = iters[r];
             info[r].converged = conv[r];
@@ -1680,6 +1686,18 @@ extern "C" int pimd_boys_dev(pimd_ctx* ctx, int n, int mord, const double* T_dev
     return PIMD_OK;
 }
 
+extern "C" int pimd_boys_f32_dev(pimd_ctx* ctx, int n, int mord, const float* T_dev, float* F_dev, int variant)
+{
+    if (!ctx || n < 0 || mord < 0 || mord > BOYS_MMAX || (variant != 0 && variant != 1) ||
+        (n > 0 && (!T_dev || !F_dev)))
+        return PIMD_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    launch_boys_eval_f32(n, mord, T_dev, F_dev, ctx->boysf, variant, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    return PIMD_OK;
+}
+
 extern "C" int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev, double* V_dev, double* evals_dev,
                              void* stream)
 {
@@ -1690,10 +1708,17 @@ extern "C" int pimd_eigh_dev(pimd_ctx* ctx, int nmat, int n, const double* A_dev
     for (int r = 0; r < nmat; r++) rm[r] = RepMat{n, 0, (long long)r * n * n};
     RepMat* d_rm;
     double* work;
+    int* nc;
     UPLOAD("eigh_rm", rm, d_rm);
     ENSURE("eigh_work", (size_t)nmat * n * n, work);
-    launch_jacobi(d_rm, nmat, A_dev, V_dev, evals_dev, n, work, nullptr, 1, ctx->stream);
+    ENSURE("eigh_nc", nmat, nc);
+    CK(cudaMemsetAsync(nc, 0, sizeof(int) * nmat, ctx->stream));
+    launch_jacobi(d_rm, nmat, A_dev, V_dev, evals_dev, n, work, nullptr, 1, ctx->stream, nc);
     CK(cudaGetLastError());
+    std::vector<int> hnc(nmat);
+    CK(cudaMemcpyAsync(hnc.data(), nc, sizeof(int) * nmat, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < nmat; r++)
+        if (hnc[r]) return set_err(ctx, PIMD_ENOTCONV, "eigensolver sweep limit reached");
     return PIMD_OK;
 }

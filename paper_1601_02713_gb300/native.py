@@ -82,6 +82,7 @@ def load(path: str | None = None):
     lib.pimd_fock_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.c_double, ctypes.c_double, _P, _P]
     lib.pimd_one_electron.argtypes = [_P, ctypes.c_int, _I, _D, _P, _D, _D, _D]
     lib.pimd_boys_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
+    lib.pimd_boys_f32_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int]
     lib.pimd_peak_bench.argtypes = [ctypes.c_int, _D, _D, _D]
     lib.pimd_eigh_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
     lib.pimd_eigh_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
@@ -287,6 +288,13 @@ def pimd_boys_dev(ctx: Context, T_dev, m: int, F_dev):
                                 _P(F_dev.data_ptr())), "pimd_boys_dev")
 
 
+def pimd_boys_f32_dev(ctx: Context, T_dev, m: int, F_dev, variant: int = 0):
+    """FP32 Boys evaluation of the mixed-precision quartets (float32 CUDA
+    tensors; variant 0 straight-line form, 1 cooperative-kernel form)."""
+    _check(load().pimd_boys_f32_dev(ctx.handle, int(T_dev.numel()), int(m), _P(T_dev.data_ptr()),
+                                    _P(F_dev.data_ptr()), int(variant)), "pimd_boys_f32_dev")
+
+
 def pimd_sad_atomic_density(ctx: Context, basis: Basis, Z: int):
     """Atomic density of element Z used by the SAD guess ([n, n] host array)."""
     n = basis.nbf([Z])
@@ -324,9 +332,36 @@ def pimd_last_stats(ctx: Context) -> dict:
     return {k: getattr(s, k) for k, _ in PimdStats._fields_}
 
 
+def eigh_args_ok(A_dev, V_dev, evals_dev) -> bool:
+    """True if A [nmat, n, n], V [nmat, n, n] and evals [nmat, n] are
+    contiguous float64 CUDA tensors on one device (checked before any launch:
+    the eigensolver reads and writes exactly these extents)."""
+    try:
+        import torch
+    except ImportError:
+        return False
+    ts = (A_dev, V_dev, evals_dev)
+    if not all(isinstance(t, torch.Tensor) for t in ts):
+        return False
+    if A_dev.dim() != 3 or A_dev.shape[1] != A_dev.shape[2]:
+        return False
+    nmat, n = int(A_dev.shape[0]), int(A_dev.shape[1])
+    if nmat <= 0 or n <= 0:
+        return False
+    if tuple(V_dev.shape) != (nmat, n, n) or tuple(evals_dev.shape) != (nmat, n):
+        return False
+    if any(t.dtype != torch.float64 or not t.is_contiguous() for t in ts):
+        return False
+    return all(t.is_cuda for t in ts) and len({t.device for t in ts}) == 1
+
+
 def pimd_eigh_dev(ctx: Context, A_dev, V_dev, evals_dev, stream: int = 0):
     """Batched symmetric eigensolver (context workspace). A, V: [nmat, n, n]
-    and evals: [nmat, n], float64 CUDA tensors."""
+    and evals: [nmat, n], contiguous float64 CUDA tensors (PimdError with
+    PIMD_EINVAL otherwise, before anything is launched)."""
+    if not eigh_args_ok(A_dev, V_dev, evals_dev):
+        raise PimdError(PIMD_EINVAL, "pimd_eigh_dev: A, V [nmat,n,n] and evals [nmat,n] must be contiguous "
+                                     "float64 CUDA tensors on one device")
     nmat, n = int(A_dev.shape[0]), int(A_dev.shape[1])
     _check(load().pimd_eigh_dev(ctx.handle, nmat, n, _P(A_dev.data_ptr()), _P(V_dev.data_ptr()),
                                 _P(evals_dev.data_ptr()), _P(stream)), "pimd_eigh_dev")
@@ -334,7 +369,12 @@ def pimd_eigh_dev(ctx: Context, A_dev, V_dev, evals_dev, stream: int = 0):
 
 def pimd_eigh_noalloc(A_dev, V_dev, evals_dev, stream: int = 0):
     """The same eigensolver without any device allocation (fixed 16 MiB
-    device workspace; nmat * n * n <= 2,097,152); returns the status code."""
+    device workspace; nmat * n * n <= 2,097,152, nmat <= 1024); it only
+    enqueues its kernels on `stream`. Returns the status code (PIMD_EINVAL,
+    without a launch, unless A, V [nmat, n, n] and evals [nmat, n] are
+    contiguous float64 CUDA tensors on one device)."""
+    if not eigh_args_ok(A_dev, V_dev, evals_dev):
+        return PIMD_EINVAL
     nmat, n = int(A_dev.shape[0]), int(A_dev.shape[1])
     return load().pimd_eigh_noalloc(nmat, n, _P(A_dev.data_ptr()), _P(V_dev.data_ptr()), _P(evals_dev.data_ptr()),
                                     _P(stream))

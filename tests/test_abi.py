@@ -115,3 +115,48 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_eigensolver_wrappers_reject_bad_tensors_without_a_launch(lib):
+    """The binding checks dtype, contiguity, shapes and device of the
+    eigensolver's tensors before calling into the library: every case here
+    is refused with PIMD_EINVAL (CPU tensors, so a call that got through would
+    fail on the device check or in the library, never silently)."""
+    torch = pytest.importorskip("torch")
+    n, nmat = 6, 2
+    A = torch.zeros(nmat, n, n, dtype=torch.float64)
+    V = torch.zeros(nmat, n, n, dtype=torch.float64)
+    w = torch.zeros(nmat, n, dtype=torch.float64)
+    bad = [
+        (A.float(), V, w),                                   # float32 input
+        (A, V.float(), w),                                   # float32 output
+        (A.transpose(1, 2), V, w),                           # strided (non-contiguous) input
+        (torch.zeros(nmat, n, n + 1, dtype=torch.float64), V, w),   # A not square
+        (A, torch.zeros(nmat, n - 1, n, dtype=torch.float64), w),   # V too small
+        (A, V, torch.zeros(nmat, n - 1, dtype=torch.float64)),      # evals too small
+        (A, V, torch.zeros(nmat - 1, n, dtype=torch.float64)),      # fewer eigenvalue rows than matrices
+        (torch.zeros(0, n, n, dtype=torch.float64), V[:0], w[:0]),  # empty batch
+        (A, V, w),                                           # valid shapes, but host tensors
+    ]
+    for args in bad:
+        assert not native.eigh_args_ok(*args)
+        assert native.pimd_eigh_noalloc(*args) == native.PIMD_EINVAL
+        with pytest.raises(native.PimdError) as ei:
+            native.pimd_eigh_dev(None, *args)
+        assert ei.value.code == native.PIMD_EINVAL
+
+
+def test_noalloc_size_limits_checked_before_any_device_call(lib):
+    """pimd_eigh_noalloc refuses sizes beyond its fixed workspace (n <= 768,
+    nmat <= 1024, nmat * n * n <= 2,097,152) before it touches the device:
+    each case is one past a limit (or empty, or a null pointer), and the
+    pointers are never dereferenced. The cases at the limits run against
+    real device buffers in the GPU tests."""
+    p = ctypes.c_void_p(16)
+    f = lib.pimd_eigh_noalloc
+    assert f(4, 768, p, p, p, None) == native.PIMD_EINVAL          # 2,359,296 doubles
+    assert f(1025, 2, p, p, p, None) == native.PIMD_EINVAL         # one descriptor too many
+    assert f(1, 769, p, p, p, None) == native.PIMD_EINVAL          # column longer than the solver holds
+    assert f(0, 4, p, p, p, None) == native.PIMD_EINVAL
+    assert f(2, 0, p, p, p, None) == native.PIMD_EINVAL
+    assert f(2, 4, None, p, p, None) == native.PIMD_EINVAL

@@ -45,6 +45,35 @@ def test_boys_function(ctx):
         assert rel.max() < 5e-14, (m, rel.max(), T[rel.argmax()])
 
 
+# FP32 Boys evaluation of the mixed-precision quartets: largest relative
+# error against the oracle (both branches: 4-term Taylor table below T = 40,
+# asymptotic form with upward recursion above, e^-T dropped from T = 72 on)
+BOYS_F32_REL = 1e-6
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_boys_function_fp32(ctx, variant):
+    """The FP32 form of F_m(T), m = 0..12, against the oracle on a dense
+    grid that straddles both switch points (T = 40: table -> asymptotic
+    branch; T = 72: e^-T dropped) and on random T up to 100. Both branches
+    stay within FP32 rounding of the recursion at the switches (the bound is
+    stated per order in BOYS_F32_REL), so no FP64 fallback is needed there."""
+    rng = np.random.default_rng(1)
+    T = np.concatenate([np.arange(38.5, 41.5, 0.002), np.arange(70.5, 73.5, 0.002), rng.uniform(0, 100, 3000),
+                        np.linspace(0, 2, 200)]).astype(np.float32)
+    Tt = torch.tensor(T, dtype=torch.float32, device="cuda")
+    Td = T.astype(np.float64)   # the reference at the float argument itself
+    for m in range(13):
+        F = torch.empty_like(Tt)
+        native.pimd_boys_f32_dev(ctx, Tt, m, F, variant)
+        got = F.cpu().numpy().astype(np.float64)
+        ref = np.array([O.boys(m, t) for t in Td])
+        rel = np.abs(got - ref) / ref
+        assert rel.max() < BOYS_F32_REL, (variant, m, rel.max(), Td[rel.argmax()])
+        near = np.abs(Td - 40.0) < 1.0
+        assert rel[near].max() < BOYS_F32_REL, (variant, m, "T near 40", rel[near].max())
+
+
 @pytest.mark.parametrize("mol", ["water", "dimer"])
 def test_one_electron_matrices(ctx, spd, mol):
     bas, B = spd

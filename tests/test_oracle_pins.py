@@ -224,6 +224,37 @@ def test_jk_matches_full_tensor(water_spd):
     np.testing.assert_allclose(K, np.einsum("mlns,ls->mn", g, D), atol=1e-11)
 
 
+@pytest.mark.parametrize("system", ["water", "dimer"])
+def test_g_block_matches_jk(water_spd, system):
+    """Every shell-pair block of the oracle's sampled Fock-block routine
+    (g_block: G = J - K/2 summed over every ordered shell pair, no screening)
+    equals J - K/2 from the canonical-quartet J/K routine, which is itself
+    pinned to the full ERI tensor above. A transposed K index, a missing 1/2
+    or a dropped permutation in g_block fails here. Water and the water dimer
+    in the s/p/d basis (d-d, d-p and cross-molecule blocks)."""
+    b = water_spd[0]
+    if system == "water":
+        Z, xyz, ob = water_spd[1], water_spd[2], water_spd[3]
+    else:
+        r, _ = I.workload("water2_min_4beads")
+        Z, c = r.stacked()
+        xyz = c[0]
+        ob = O.OracleBasis.build(b, Z, xyz)
+    N = ob.nbf
+    rng = np.random.default_rng(11)
+    D = rng.normal(size=(N, N))
+    D = D + D.T
+    J, K, _ = O.jk(ob, D, 0.0)
+    G = J - 0.5 * K
+    off = np.cumsum([0] + [ob.shell_nbf(s) for s in range(len(ob.l))])
+    scale = np.abs(G).max()
+    for a in range(len(ob.l)):
+        for bb in range(len(ob.l)):
+            blk = O.g_block(ob, D, a, bb)
+            ref = G[off[a]:off[a + 1], off[bb]:off[bb + 1]]
+            assert np.abs(blk - ref).max() <= 1e-12 * scale, (system, a, bb)
+
+
 # ---------------------------------------------------------------- full RHF
 def _rot(axis, ang):
     axis = np.asarray(axis, float) / np.linalg.norm(axis)
