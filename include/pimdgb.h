@@ -74,6 +74,9 @@ typedef struct {
                              (density increment + Fock build; Fock assembly, energy and DIIS error;
                              DIIS extrapolation + diagonalisation + density) is replayed as three
                              CUDA graphs captured from the first; 0: plain launches */
+    int full_every;       /* 8: after this many SCF iterations without one, the Fock build is a full
+                             build (G'(D)) instead of the incremental G' += G'(D - D_prev); 1: every
+                             build full. Convergence is only accepted on a full build. */
 } pimd_scf_opts;
 
 /* Per-replica result record. */
@@ -162,6 +165,13 @@ typedef struct {
     double eris32_per_build;     /* the part of eris_per_build evaluated in FP32 */
 } pimd_stats;
 int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
+
+/* SCF convergence record of replica `rep` in the last forces call: per SCF
+ * iteration k < min(returned count, maxit), energy[k] (hartree, the energy of
+ * that iteration's Fock build), error[k] (max |X^T (FDS - SDF) X|) and
+ * full_build[k] (1 full Fock build, 0 incremental). Any output may be NULL.
+ * Returns the number of iterations of the replica, or a negative error. */
+int pimd_last_trace(const pimd_ctx* ctx, int rep, int maxit, double* energy, double* error, int* full_build);
 
 /* Testing hooks (same kernels as the forces path):
  * pimd_fock_dev: for nrep replicas of one molecule and a given density

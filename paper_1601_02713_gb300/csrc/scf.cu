@@ -111,6 +111,12 @@ struct pimd_ctx {
     int grad_var[64];
     // SAD guess: atomic densities per (basis uid, Z), row-major nbf x nbf
     std::map<std::pair<long long, int>, std::vector<double>> sad;
+    // SCF record of the last call: per replica, per iteration (E, error, full build)
+    struct TraceRow {
+        double E, err;
+        int full;
+    };
+    std::vector<std::vector<TraceRow>> trace;
 };
 
 static int set_err(pimd_ctx* ctx, int code, const std::string& msg)
@@ -183,6 +189,7 @@ extern "C" void pimd_scf_opts_default(pimd_scf_opts* o)
     o->deterministic = 0;
     o->want_gradient = 1;
     o->use_graphs = 1;
+    o->full_every = 8;
 }
 
 extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
@@ -340,6 +347,20 @@ extern "C" const char* pimd_strerror(int code)
         case PIMD_EBASIS: return "overlap matrix numerically singular";
         default: return "unknown error";
     }
+}
+
+extern "C" int pimd_last_trace(const pimd_ctx* ctx, int rep, int maxit, double* energy, double* error,
+                               int* full_build)
+{
+    if (!ctx || rep < 0 || maxit < 0) return PIMD_EINVAL;
+    if (rep >= (int)ctx->trace.size()) return PIMD_EINVAL;
+    const auto& t = ctx->trace[rep];
+    for (int k = 0; k < (int)t.size() && k < maxit; k++) {
+        if (energy) energy[k] = t[k].E;
+        if (error) error[k] = t[k].err;
+        if (full_build) full_build[k] = t[k].full;
+    }
+    return (int)t.size();
 }
 
 extern "C" int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out)
@@ -1156,7 +1177,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     std::vector<double> fdE(nrep, 0.0), ferr(nrep, 0.0);
     // build mode per replica: 2 full Fock build, 1 incremental (G' += G'(D - D_prev))
     std::vector<int> mode(nrep, 2), since_full(nrep, 0);
-    const int full_every = 8;
+    const int full_every = o->full_every > 0 ? o->full_every : 8;
+    ctx->trace.assign(nrep, {});
     int nactive = nrep;
     const bool graphs = o->use_graphs != 0;
     GraphSeg seg_fock, seg_err, seg_diag;
@@ -1211,6 +1233,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             iters[r] = it;
             fdE[r] = it > 1 ? fabs(E[r] - Eprev[r]) : INFINITY;
             ferr[r] = emax[r];
+            ctx->trace[r].push_back({E[r], emax[r], mode[r] == 2 ? 1 : 0});
             const bool met = it > 1 && fdE[r] < o->conv_energy && emax[r] < o->conv_error;
             // convergence is only accepted on a full (non-incremental) build
             if (met && mode[r] == 2) {
@@ -1370,7 +1393,7 @@ static int check_common(pimd_ctx* ctx, const pimd_basis* basis, const pimd_scf_o
         memcpy(&o, opts, opts->struct_size);
     }
     if (!(o.conv_energy > 0) || !(o.conv_error > 0) || o.max_iter < 1 || o.max_iter > 10000 ||
-        !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 5)
+        !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 5 || o.full_every < 0)
         return set_err(ctx, PIMD_EINVAL, "bad SCF options");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
     return PIMD_OK;

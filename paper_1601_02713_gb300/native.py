@@ -21,7 +21,8 @@ class PimdScfOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("conv_energy", ctypes.c_double),
                 ("conv_error", ctypes.c_double), ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int),
                 ("schwarz_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("guess", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("want_gradient", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("want_gradient", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("full_every", ctypes.c_int)]
 
 
 class PimdInfo(ctypes.Structure):
@@ -79,6 +80,7 @@ def load(path: str | None = None):
     lib.string_images_forces_dev.argtypes = [_P, ctypes.c_int, _I, _I, _P, _P, ctypes.POINTER(PimdScfOpts), _P, _P,
                                              ctypes.POINTER(PimdInfo), _P]
     lib.pimd_last_stats.argtypes = [_P, ctypes.POINTER(PimdStats)]
+    lib.pimd_last_trace.argtypes = [_P, ctypes.c_int, ctypes.c_int, _D, _D, _I]
     lib.pimd_fock_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.c_double, ctypes.c_double, _P, _P]
     lib.pimd_one_electron.argtypes = [_P, ctypes.c_int, _I, _D, _P, _D, _D, _D]
     lib.pimd_boys_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
@@ -324,6 +326,18 @@ def pimd_bf16_gemm_dev(A, B, C, ta: bool, tb: bool, stream: int = 0) -> int:
     K = int(A.shape[0] if ta else A.shape[1])
     return load().pimd_bf16_gemm_dev(M, N, K, _P(A.data_ptr()), int(A.stride(0)), int(ta), _P(B.data_ptr()),
                                      int(B.stride(0)), int(tb), _P(C.data_ptr()), int(C.stride(0)), _P(stream))
+
+
+def pimd_last_trace(ctx: Context, rep: int) -> dict:
+    """Per-iteration energy, error and full-build flag of replica rep in the
+    last forces call."""
+    lib = load()
+    n = lib.pimd_last_trace(ctx.handle, int(rep), 0, None, None, None)
+    if n < 0:
+        raise PimdError(n, "pimd_last_trace")
+    E, err, full = np.zeros(max(n, 1)), np.zeros(max(n, 1)), np.zeros(max(n, 1), np.int32)
+    lib.pimd_last_trace(ctx.handle, int(rep), n, _dp(E), _dp(err), _ip(full))
+    return {"energy": E[:n], "error": err[:n], "full_build": full[:n]}
 
 
 def pimd_last_stats(ctx: Context) -> dict:
