@@ -55,7 +55,7 @@ typedef struct {
     double conv_energy;   /* |E_k - E_{k-1}| threshold, 1e-10 hartree */
     double conv_error;    /* max |X^T (FDS - SDF) X| threshold, 1e-8 */
     int max_iter;         /* 64 */
-    int diis_size;        /* 8 (Pulay subspace, 2..8) */
+    int diis_size;        /* 8 (Pulay subspace, 2..16) */
     double schwarz_tau;   /* 1e-12: quartets with Q_ab Q_cd below it are skipped (Sec. 3.1) */
     double fp32_tau;      /* 0: all quartets in FP64; > schwarz_tau: quartets whose bound
                              Q_ab Q_cd max|D block| is below it (D: the density increment of an
@@ -77,6 +77,14 @@ typedef struct {
     int full_every;       /* 8: after this many SCF iterations without one, the Fock build is a full
                              build (G'(D)) instead of the incremental G' += G'(D - D_prev); 1: every
                              build full. Convergence is only accepted on a full build. */
+    double prim_screen;   /* 1/81: within a screened shell quartet, primitive quartets whose bound
+                             qp_ij qp_kl max|D block| (qp: Schwarz factor of one primitive pair) is
+                             below schwarz_tau * prim_screen are skipped in the Fock build (at most
+                             81 per quartet, so their sum stays below schwarz_tau); 0 keeps all */
+    int reuse_mode;       /* start of a replica from its previous call (guess 1, 3, 5): 0 the density
+                             2 C_occ C_occ^T of the cached MOs; 1 that density after two McWeeny
+                             purification steps in the new overlap metric; 2 the aufbau density of
+                             the cached Fock matrix diagonalised in the new orthogonal basis */
 } pimd_scf_opts;
 
 /* Per-replica result record. */

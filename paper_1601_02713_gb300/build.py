@@ -137,7 +137,7 @@ def generate_sources():
         e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
               "                     const double* D, const float* Df, double* G, const double* boys,",
               "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
-              "                     unsigned long long* cnt, int bs, cudaStream_t st)",
+              "                     unsigned long long* cnt, int bs, double tp, cudaStream_t st)",
               "{",
               "    if (ntiles <= 0) return;",
               "    const double split = fp32_tau > tau ? fp32_tau : tau;"]
@@ -146,24 +146,30 @@ def generate_sources():
                   "        CoopTape t; int W, Wf; size_t bytes, bytesf;",
                   f"        coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
                   f"        jk_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles,",
-                  "            D, G, boys, split, 1e300, Dsh, cnt, t);",
+                  "            D, G, boys, split, 1e300, Dsh, cnt, t, tp);",
                   "        if (fp32_tau > tau)",
                   f"            jk_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S, R,",
-                  "                tiles, Df, G, boysf, tau, fp32_tau, Dsh, cnt + 2, t);",
+                  "                tiles, Df, G, boysf, tau, fp32_tau, Dsh, cnt + 2, t, tp);",
                   "        return;",
                   "    }"]
         if straight_e[nm]:
             e += ["    const int b = bs > 0 ? bs : 128;",
-                  f"    jk_kernel<Cls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt);",
+                  f"    jk_kernel<Cls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt,",
+                  "                                                      tp);",
                   "    if (fp32_tau > tau)",
                   f"        jk_kernel<Cls_{nm}, float><<<ntiles, b, 0, st>>>(P, S, R, tiles, Df, G, boysf, tau, fp32_tau, Dsh,",
-                  "                                                       cnt + 2);"]
+                  "                                                       cnt + 2, tp);"]
         e.append("}")
         if same:
             e += [f"void launch_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
                   "                          const double* boys, double* Q, cudaStream_t st)",
                   "{",
                   f"    if (n > 0) schwarz_kernel<Cls_{nm}><<<(n + 127) / 128, 128, 0, st>>>(P, S, list, n, boys, Q);",
+                  "}",
+                  f"void launch_prim_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
+                  "                               const double* boys, double* pp, float* qp, cudaStream_t st)",
+                  "{",
+                  f"    if (n > 0) prim_schwarz_kernel<Cls_{nm}><<<(n + 127) / 128, 128, 0, st>>>(P, S, list, n, boys, pp, qp);",
                   "}"]
         e.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_eri_{nm}.cu")
@@ -211,14 +217,17 @@ def generate_sources():
     # dispatch
     d = ['#include "internal.h"', "namespace pimd {"]
     sig_jk = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, const float*, double*, "
-              "const double*, const float*, double, double, const double*, unsigned long long*, int, cudaStream_t")
+              "const double*, const float*, double, double, const double*, unsigned long long*, int, double, "
+              "cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
+    sig_psw = "const Pairs&, const Shells&, const int*, int, const double*, double*, float*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
              "const float*, double, double, const double*, int, int, cudaStream_t")
     for c, nm in zip(classes, names):
         d.append(f"void launch_jk_{nm}({sig_jk});")
         if (c[0], c[1]) == (c[2], c[3]):
             d.append(f"void launch_schwarz_{nm}({sig_sw});")
+            d.append(f"void launch_prim_schwarz_{nm}({sig_psw});")
         d.append(f"void launch_grad2e_{nm}({sig_g});")
         d.append(f"void grad2e_upload_{nm}();")
     d.append(f"int n_class_pairs() {{ return {len(classes)}; }}")
@@ -242,8 +251,8 @@ def generate_sources():
     d.append("static const JkFn jk_tab[] = {" + ", ".join(f"launch_jk_{nm}" for nm in names) + "};")
     d.append("void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau, "
-             "double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, cudaStream_t st)")
-    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, bs, st); }")
+             "double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, double tau_prim, cudaStream_t st)")
+    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, bs, tau_prim, st); }")
     for fn, tab in (("class_pair_coop", coop_e), ("class_pair_straight", straight_e), ("grad_pair_coop", coop_g),
                     ("grad_pair_straight", {nm: not heavy[nm] for nm in names})):
         d.append(f"bool {fn}(int cp)")
@@ -257,6 +266,11 @@ def generate_sources():
     d.append("void launch_schwarz(int X, const Pairs& P, const Shells& S, const int* list, int n, const double* boys, "
              "double* Q, cudaStream_t st)")
     d.append("{ sw_tab[X](P, S, list, n, boys, Q, st); }")
+    d.append(f"typedef void (*PswFn)({sig_psw});")
+    d.append("static const PswFn psw_tab[] = {" + ", ".join(f"launch_prim_schwarz_{nm}" for nm in same) + "};")
+    d.append("void launch_prim_schwarz(int X, const Pairs& P, const Shells& S, const int* list, int n, "
+             "const double* boys, double* pp, float* qp, cudaStream_t st)")
+    d.append("{ psw_tab[X](P, S, list, n, boys, pp, qp, st); }")
     d.append(f"typedef void (*GFn)({sig_g});")
     d.append("static const GFn g_tab[] = {" + ", ".join(f"launch_grad2e_{nm}" for nm in names) + "};")
 

@@ -119,18 +119,27 @@ __device__ __forceinline__ void coop_prim(const Pairs& P, int ab, int cd, int k,
 }
 
 // contracted accumulators of one quartet: zero, then every primitive quartet
-// through the VRR and the accumulation ops
+// through the VRR and the accumulation ops. Primitive quartets (i|j) with
+// qp_i qp_j < qthr are skipped (qthr <= 0: none); returns the number evaluated.
 template <typename R>
-__device__ __forceinline__ void coop_primitive_loop(const CoopTape& tp, const Pairs& P, int ab, int cd,
-                                                    const R* __restrict__ boys, R* sm, R* geom, int lane)
+__device__ __forceinline__ int coop_primitive_loop(const CoopTape& tp, const Pairs& P, int ab, int cd,
+                                                   const R* __restrict__ boys, R* sm, R* geom, int lane,
+                                                   float qthr = 0.0f)
 {
     const int NG = COOP_NG0 + tp.L + 1;
     for (int i = lane; i < tp.NACC; i += 32) sm[i] = R(0);
     const int nab = P.npp[ab], npq = nab * P.npp[cd];
+    int done = 0;
     for (int base = 0; base < npq; base += 32) {
-        if (base + lane < npq) coop_prim<R>(P, ab, cd, base + lane, nab, tp.L, boys, geom + lane * NG);
+        const int k = base + lane;
+        bool keep = k < npq;
+        if (keep && qthr > 0.0f)
+            keep = __ldg(P.qp + (size_t)(k % nab) * P.n + ab) * __ldg(P.qp + (size_t)(k / nab) * P.n + cd) >= qthr;
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (keep) coop_prim<R>(P, ab, cd, k, nab, tp.L, boys, geom + __popc(mask & ((1u << lane) - 1u)) * NG);
         __syncwarp();
-        const int nb = min(32, npq - base);
+        const int nb = __popc(mask);
+        done += nb;
         for (int p = 0; p < nb; p++) {
             const R* g = geom + p * NG;
             if (lane <= tp.L) sm[tp.F0 + lane] = g[COOP_NG0 + lane];
@@ -144,6 +153,7 @@ __device__ __forceinline__ void coop_primitive_loop(const CoopTape& tp, const Pa
             __syncwarp();
         }
     }
+    return done;
 }
 
 // one index of a block between Cartesian (nc) and spherical (ns) d components,
@@ -269,7 +279,8 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
                                                       const Rt* __restrict__ Dall, double* __restrict__ Gall,
                                                       const Rt* __restrict__ boys, double tau_lo, double tau_hi,
                                                       const double* __restrict__ Dsh,
-                                                      unsigned long long* __restrict__ cnt, CoopTape tp)
+                                                      unsigned long long* __restrict__ cnt, CoopTape tp,
+                                                      double tau_prim)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Rt* smem = (Rt*)smem_raw;
@@ -296,16 +307,16 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
                                fmax(shell_bound(R, Dsh, r, sb, sc), shell_bound(R, Dsh, r, sb, sd)));
         const double bound = P.Q[ab] * P.Q[cd] * dq;
         if (bound < tau_lo || bound >= tau_hi) continue;
-        if (lane == 0) {
-            atomicAdd(cnt, 1ull);
-            atomicAdd(cnt + 1, (unsigned long long)(P.npp[ab] * P.npp[cd]));
-        }
         double Cc[3], Dd[3];
         for (int x = 0; x < 3; x++) {
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, lane);
+        const int nprim = coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, lane, (float)(tau_prim / dq));
+        if (lane == 0) {
+            atomicAdd(cnt, 1ull);
+            atomicAdd(cnt + 1, (unsigned long long)nprim);
+        }
         const Rt AB[3] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2])};
         const Rt CD[3] = {Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
         coop_hrr<Rt>(tp, 0, sm, AB, CD, lane);

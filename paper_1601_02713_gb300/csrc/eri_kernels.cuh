@@ -144,11 +144,47 @@ __device__ __forceinline__ void prim_quartet(const R* bra, const R* ket, PrimQ<R
 
 __device__ __forceinline__ double atomic_add_d(double* a, double v) { return atomicAdd(a, v); }
 
+// J'_ab of a tile: every lane of the warp holds a quartet with the same bra
+// pair (ab), so the bra-side Coulomb block sum_cd 2f D_cd (ab|cd) is summed
+// over the warp with shuffles and added to G' with one atomic per element
+// (lanes without a quartet contribute zero; all 32 lanes must call this).
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void bra_coulomb_warp(const R* __restrict__ I, double f, bool work, int fa, int fb,
+                                                 int fc, int fd, int N, const R* __restrict__ D,
+                                                 double* __restrict__ G)
+{
+    constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
+    R Dcd[nc * nd];
+#pragma unroll
+    for (int i = 0; i < nc; i++)
+#pragma unroll
+        for (int j = 0; j < nd; j++) Dcd[i * nd + j] = work ? __ldg(D + (size_t)(fc + i) * N + fd + j) : R(0);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < na; a++) {
+#pragma unroll
+        for (int b = 0; b < nb; b++) {
+            R s = R(0);
+#pragma unroll
+            for (int c = 0; c < nc; c++)
+#pragma unroll
+                for (int d = 0; d < nd; d++) s += Dcd[c * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
+            double v = work ? 2.0 * f * (double)s : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && v != 0.0) atomic_add_d(G + (size_t)(fa + a) * N + fb + b, v);
+        }
+    }
+}
+
 // Contract a spherical block with the density and scatter into G' (the
-// contraction in the block's precision R, the accumulation in FP64).
+// contraction in the block's precision R, the accumulation in FP64): J'_cd
+// and the four exchange blocks; with bra_j, also J'_ab (else the caller adds
+// it with bra_coulomb_warp).
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, int fa, int fb, int fc, int fd,
-                                           int N, const R* __restrict__ D, double* __restrict__ G)
+                                           int N, const R* __restrict__ D, double* __restrict__ G,
+                                           bool bra_j = true)
 {
     constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
     R Dab[na * nb], Dcd[nc * nd], Dac[na * nc], Dad[na * nd], Dbc[nb * nc], Dbd[nb * nd];
@@ -177,17 +213,19 @@ __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, in
 #pragma unroll
         for (int j = 0; j < nd; j++) Dbd[i * nd + j] = __ldg(D + (size_t)(fb + i) * N + fd + j);
 
-    // J'_ab and K'_ac, K'_ad (rows of the bra)
+    // J'_ab (rows of the bra)
+    if (bra_j) {
 #pragma unroll
-    for (int a = 0; a < na; a++) {
+        for (int a = 0; a < na; a++) {
 #pragma unroll
-        for (int b = 0; b < nb; b++) {
-            R s = R(0);
+            for (int b = 0; b < nb; b++) {
+                R s = R(0);
 #pragma unroll
-            for (int c = 0; c < nc; c++)
+                for (int c = 0; c < nc; c++)
 #pragma unroll
-                for (int d = 0; d < nd; d++) s += Dcd[c * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s);
+                    for (int d = 0; d < nd; d++) s += Dcd[c * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
+                atomic_add_d(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s);
+            }
         }
     }
 #pragma unroll
@@ -263,20 +301,30 @@ __device__ __forceinline__ void load_ppn(const Pairs& P, int g, int k, float* ou
 __device__ __forceinline__ const double* pp_base(const Pairs& P, double) { return P.pp; }
 __device__ __forceinline__ const float* pp_base(const Pairs& P, float) { return P.ppf; }
 
-// contracted Cartesian block of one quartet via the generated recursion
+// contracted Cartesian block of one quartet via the generated recursion.
+// Primitive screening: primitive quartet (i|j) is skipped when
+// qp_i qp_j < qthr (qthr = the primitive cutoff over the quartet's density
+// bound; qthr <= 0 keeps every primitive); both primitive lists are in
+// descending order of qp, so each loop stops at its first skipped entry.
+// Returns the number of primitive quartets evaluated.
 template <class C, typename R>
-__device__ __forceinline__ void quartet_cart(const R (*sbra)[PIMD_MAXPP], int nbra, const Pairs& P, int cd,
-                                             const double A[3], const double B[3], const double Cc[3],
-                                             const double Dd[3], const R* __restrict__ boys, R* cart)
+__device__ __forceinline__ int quartet_cart(const R (*sbra)[PIMD_MAXPP], const float* sqp, int nbra, const Pairs& P,
+                                            int cd, const double A[3], const double B[3], const double Cc[3],
+                                            const double Dd[3], const R* __restrict__ boys, float qthr, R* cart)
 {
     R acc[C::NE * C::NF];
 #pragma unroll
     for (int i = 0; i < C::NE * C::NF; i++) acc[i] = R(0);
     const int nket = P.npp[cd];
+    int nprim = 0;
     for (int j = 0; j < nket; j++) {
+        const float qj = qthr > 0.0f ? __ldg(P.qp + (size_t)j * P.n + cd) : 1.0f;
+        if (qj * sqp[0] < qthr) break;
         R ket[PP_NERI];
         load_ppn(P, cd, j, ket, PP_NERI);
         for (int i = 0; i < nbra; i++) {
+            if (sqp[i] * qj < qthr) break;
+            nprim++;
             R bra[PP_NERI];
 #pragma unroll
             for (int f = 0; f < PP_NERI; f++) bra[f] = sbra[f][i];
@@ -290,6 +338,7 @@ __device__ __forceinline__ void quartet_cart(const R (*sbra)[PIMD_MAXPP], int nb
     }
     C::template hrr<R>(acc, R(A[0] - B[0]), R(A[1] - B[1]), R(A[2] - B[2]), R(Cc[0] - Dd[0]), R(Cc[1] - Dd[1]),
                        R(Cc[2] - Dd[2]), cart);
+    return nprim;
 }
 
 // Fock (G') build over the quartets of one class pair whose density-weighted
@@ -297,13 +346,17 @@ __device__ __forceinline__ void quartet_cart(const R (*sbra)[PIMD_MAXPP], int nb
 // the small quartets of the mixed mode). blockDim.x == the tile's ket width
 // (32, 64 or 128, chosen per class pair by the autotuner).
 // cnt: executed quartets and primitive quartets.
+// tau_prim: primitive quartets whose bound qp_i qp_j (density bound) is below
+// it are skipped (0 keeps every primitive quartet).
 template <class C, typename R>
 __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, const Tile* __restrict__ tiles,
                                                  const R* __restrict__ Dall, double* __restrict__ Gall,
                                                  const R* __restrict__ boys, double tau_lo, double tau_hi,
-                                                 const double* __restrict__ Dsh, unsigned long long* __restrict__ cnt)
+                                                 const double* __restrict__ Dsh, unsigned long long* __restrict__ cnt,
+                                                 double tau_prim)
 {
     __shared__ R sbra[PP_NERI][PIMD_MAXPP];
+    __shared__ float sqp[PIMD_MAXPP];
     const Tile t = tiles[blockIdx.x];
     if (!R_.active[t.rep]) return;
     const int ab = t.ab;
@@ -311,11 +364,13 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
         const int f = e / PIMD_MAXPP, k = e % PIMD_MAXPP;
         sbra[f][k] = pp_base(P, R(0))[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     }
+    if (threadIdx.x < PIMD_MAXPP) sqp[threadIdx.x] = P.qp[(size_t)threadIdx.x * P.n + ab];
     __syncthreads();
     const int cd = t.c0 + threadIdx.x;
     const int r = t.rep;
     bool work = cd < t.c1;
     int sa = 0, sb = 0, sc = 0, sd = 0;
+    float qthr = 0.0f;
     if (work) {
         sa = P.sa[ab];
         sb = P.sb[ab];
@@ -328,34 +383,44 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
                                fmax(shell_bound(R_, Dsh, r, sb, sc), shell_bound(R_, Dsh, r, sb, sd)));
         const double bound = P.Q[ab] * P.Q[cd] * dq;
         work = bound >= tau_lo && bound < tau_hi;
+        qthr = (float)(tau_prim / dq);
+    }
+    // a warp with no quartet left leaves; otherwise every lane stays for the
+    // warp-wide J'_ab sum (the block's warps share the bra pair)
+    if (__all_sync(0xffffffffu, !work)) return;
+    constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
+    R cart[NCART], tmp[NCART];
+    double f = 0.0;
+    int nprim = 0;
+    if (work) {
+        double A[3], B[3], Cc[3], Dd[3];
+#pragma unroll
+        for (int x = 0; x < 3; x++) {
+            A[x] = S.xyz[3 * sa + x];
+            B[x] = S.xyz[3 * sb + x];
+            Cc[x] = S.xyz[3 * sc + x];
+            Dd[x] = S.xyz[3 * sd + x];
+        }
+        nprim = quartet_cart<C, R>(sbra, sqp, P.npp[ab], P, cd, A, B, Cc, Dd, boys, qthr, cart);
+        cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
+        f = 1.0;
+        if (sa == sb) f *= 0.5;
+        if (sc == sd) f *= 0.5;
+        if (ab == cd) f *= 0.5;
     }
     const unsigned nq = __reduce_add_sync(0xffffffffu, work ? 1u : 0u);
-    const unsigned np = __reduce_add_sync(0xffffffffu, work ? (unsigned)(P.npp[ab] * P.npp[cd]) : 0u);
+    const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)nprim);
     if ((threadIdx.x & 31) == 0 && nq) {
         atomicAdd(cnt, (unsigned long long)nq);
         atomicAdd(cnt + 1, (unsigned long long)np);
     }
-    if (!work) return;
-    double A[3], B[3], Cc[3], Dd[3];
-#pragma unroll
-    for (int x = 0; x < 3; x++) {
-        A[x] = S.xyz[3 * sa + x];
-        B[x] = S.xyz[3 * sb + x];
-        Cc[x] = S.xyz[3 * sc + x];
-        Dd[x] = S.xyz[3 * sd + x];
-    }
-    constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
-    R cart[NCART], tmp[NCART];
-    quartet_cart<C, R>(sbra, P.npp[ab], P, cd, A, B, Cc, Dd, boys, cart);
-    cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
-    double f = 1.0;
-    if (sa == sb) f *= 0.5;
-    if (sc == sd) f *= 0.5;
-    if (ab == cd) f *= 0.5;
     const int N = R_.nbf[r];
     const size_t off = R_.moff[r];
-    scatter_jk<C::LA, C::LB, C::LC, C::LD, R>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
-                                              Gall + off);
+    bra_coulomb_warp<C::LA, C::LB, C::LC, C::LD, R>(cart, f, work, S.bf[P.sa[ab]], S.bf[P.sb[ab]], S.bf[sc],
+                                                     S.bf[sd], N, Dall + off, Gall + off);
+    if (work)
+        scatter_jk<C::LA, C::LB, C::LC, C::LD, R>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
+                                                  Gall + off, false);
 }
 
 // Schwarz factors: Q_ab = sqrt(max over functions of (mn|mn)), one thread per pair
@@ -379,7 +444,8 @@ __global__ void __launch_bounds__(128) schwarz_kernel(Pairs P, Shells S, const i
     }
     constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
     double cart[NCART], tmp[NCART];
-    quartet_cart<C, double>(sbra_l, np, P, ab, A, B, A, B, boys, cart);
+    const float qone[PIMD_MAXPP] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+    quartet_cart<C, double>(sbra_l, qone, np, P, ab, A, B, A, B, boys, 0.0f, cart);
     cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
     constexpr int na = nsph(C::LA), nb = nsph(C::LB);
     double m = 0.0;
@@ -388,6 +454,72 @@ __global__ void __launch_bounds__(128) schwarz_kernel(Pairs P, Shells S, const i
 #pragma unroll
         for (int j = 0; j < nb; j++) m = fmax(m, fabs(cart[((i * nb + j) * na + i) * nb + j]));
     Qout[ab] = sqrt(m);
+}
+
+// Primitive-pair Schwarz factors: for every primitive pair k of shell pair ab
+// (one thread per pair), qp_k = sqrt(max over functions of |(kk|kk)|) with
+// the contraction coefficients included, so that |(ij|kl)| <= qp_i qp_l for
+// any primitive quartet (Cauchy-Schwarz for the two charge distributions).
+// The pair's primitive data are then reordered by descending qp (every field,
+// in place) and qp is stored in that order.
+template <class C>
+__global__ void __launch_bounds__(128) prim_schwarz_kernel(Pairs P, Shells S, const int* __restrict__ list, int n,
+                                                           const double* __restrict__ boys, double* pp, float* qp)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int ab = list[idx];
+    const int sa = P.sa[ab], sb = P.sb[ab];
+    const int np = P.npp[ab];
+    const size_t N = P.n;
+    double A[3], B[3];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        A[x] = S.xyz[3 * sa + x];
+        B[x] = S.xyz[3 * sb + x];
+    }
+    constexpr int na = nsph(C::LA), nb = nsph(C::LB);
+    constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
+    float q[PIMD_MAXPP];
+    int perm[PIMD_MAXPP];
+    for (int k = 0; k < np; k++) {
+        double v[PP_NERI];
+        for (int f = 0; f < PP_NERI; f++) v[f] = pp[((size_t)f * PIMD_MAXPP + k) * N + ab];
+        double acc[C::NE * C::NF];
+        for (int i = 0; i < C::NE * C::NF; i++) acc[i] = 0.0;
+        PrimQ<double> g;
+        prim_quartet<double>(v, v, g);
+        double F[C::L + 1];
+        boys_eval<C::L>(g.T, boys, g.theta, F);
+        C::template vrr<double>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1],
+                                g.QC[2], g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, acc);
+        double cart[NCART], tmp[NCART];
+        C::template hrr<double>(acc, A[0] - B[0], A[1] - B[1], A[2] - B[2], A[0] - B[0], A[1] - B[1], A[2] - B[2],
+                                cart);
+        cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
+        double m = 0.0;
+        for (int i = 0; i < na; i++)
+            for (int j = 0; j < nb; j++) m = fmax(m, fabs(cart[((i * nb + j) * na + i) * nb + j]));
+        // rounded up so that the float bound stays an upper bound
+        q[k] = __double2float_ru(sqrt(m) * (1.0 + 1e-6));
+        perm[k] = k;
+    }
+    // insertion sort of the primitive pairs, descending qp (stable)
+    for (int k = 1; k < np; k++) {
+        const int pk = perm[k];
+        int j = k - 1;
+        while (j >= 0 && q[perm[j]] < q[pk]) {
+            perm[j + 1] = perm[j];
+            j--;
+        }
+        perm[j + 1] = pk;
+    }
+    for (int f = 0; f < PP_NF; f++) {
+        double v[PIMD_MAXPP];
+        for (int k = 0; k < np; k++) v[k] = pp[((size_t)f * PIMD_MAXPP + k) * N + ab];
+        for (int k = 0; k < np; k++) pp[((size_t)f * PIMD_MAXPP + k) * N + ab] = v[perm[k]];
+    }
+    for (int k = 0; k < PIMD_MAXPP; k++) qp[(size_t)k * N + ab] = k < np ? q[perm[k]] : 0.0f;
 }
 
 }  // namespace pimd

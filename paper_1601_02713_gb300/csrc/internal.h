@@ -56,9 +56,11 @@ long long class_vrr_flops(int cp);
 // bs = threads per block = the tiles' ket width for the straight-line
 // kernel, bs = 0 for the warp-cooperative kernel (a class with one variant
 // ignores the choice)
+// tau_prim: primitive quartets with qp_i qp_j max|D block| below it are skipped (0: none)
 void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau,
-               double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, cudaStream_t st);
+               double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, double tau_prim,
+               cudaStream_t st);
 // kernel variants generated for a class pair: the warp-cooperative tape
 // kernel and the straight-line kernel, for the Fock build and the gradient
 bool class_pair_coop(int cp);
@@ -67,6 +69,10 @@ bool grad_pair_coop(int cp);
 bool grad_pair_straight(int cp);
 void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n, const double* boys,
                     double* Q, cudaStream_t st);
+// primitive-pair Schwarz factors qp of the listed pairs of one class; reorders
+// each pair's primitive data in pp by descending qp
+void launch_prim_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n,
+                         const double* boys, double* pp, float* qp, cudaStream_t st);
 // two-electron gradient of class pair cp: quartets with bound Q_ab Q_cd |Gamma|
 // >= max(tau, fp32_tau) in FP64, those in [tau, fp32_tau) in FP32; variant 0
 // the warp-cooperative kernel, 1 the straight-line kernel with bs threads per

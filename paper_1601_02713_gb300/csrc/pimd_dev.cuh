@@ -53,6 +53,9 @@ struct Pairs {
     const double* pp;     // SoA primitive-pair data
     const double* Q;      // Schwarz factor sqrt(max |(ab|ab)|)
     const float* ppf;     // FP32 copy of pp (mixed-precision quartets)
+    const float* qp;      // qp[k * n + g]: Schwarz factor sqrt(max |(ij|ij)|) of primitive pair k alone
+                          // (contraction coefficients included); the primitive pairs of every shell
+                          // pair are stored in descending order of it
 };
 
 struct Reps {

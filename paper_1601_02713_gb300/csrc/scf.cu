@@ -97,7 +97,8 @@ struct pimd_ctx {
     struct MO {
         std::vector<int> Z;
         int N = 0;
-        DevBuf C;
+        DevBuf C;   // MO coefficients of the replica's last call
+        DevBuf F;   // its final Fock matrix (AO basis)
     };
     std::vector<MO> mo;
     cudaEvent_t ev[8];
@@ -190,6 +191,8 @@ extern "C" void pimd_scf_opts_default(pimd_scf_opts* o)
     o->want_gradient = 1;
     o->use_graphs = 1;
     o->full_every = 8;
+    o->prim_screen = 1.0 / 81.0;
+    o->reuse_mode = 0;
 }
 
 extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
@@ -231,8 +234,10 @@ extern "C" void pimd_ctx_destroy(pimd_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
-    for (auto& m : ctx->mo)
+    for (auto& m : ctx->mo) {
         if (m.C.p) cudaFree(m.C.p);
+        if (m.F.p) cudaFree(m.F.p);
+    }
     if (ctx->boys) cudaFree(ctx->boys);
     if (ctx->boysf) cudaFree(ctx->boysf);
     for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
@@ -571,7 +576,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     ENSURE("npp", npair, d_npp);
     ENSURE("pp", (size_t)PP_NF * PIMD_MAXPP * npair, d_pp);
     ENSURE("Q", npair, d_Q);
-    bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, nullptr};
+    bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, nullptr, nullptr};
     launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
     ctx->stats.kernel_launches += 2;
     for (int X = 0; X < 6; X++) {
@@ -622,8 +627,22 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
         UPLOAD("Q", Q, d_Q);
         float* d_ppf;
         ENSURE("ppf", (size_t)PP_NF * PIMD_MAXPP * npair, d_ppf);
-        bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, d_ppf};
+        float* d_qp;
+        ENSURE("qp", (size_t)PIMD_MAXPP * npair, d_qp);
+        bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, d_ppf, d_qp};
         launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
+        // primitive-pair bounds, and each pair's primitives in descending order of them
+        for (int X = 0; X < 6; X++) {
+            std::vector<int> list;
+            for (int r = 0; r < nrep; r++)
+                for (int g = bt.grp0[r * 6 + X]; g < bt.grp0[r * 6 + X + 1]; g++) list.push_back(g);
+            if (list.empty()) continue;
+            int* d_list;
+            std::string nm = "psw_list" + std::to_string(X);
+            UPLOAD(nm.c_str(), list, d_list);
+            launch_prim_schwarz(X, bt.P, bt.S, d_list, (int)list.size(), ctx->boys, d_pp, d_qp, ctx->stream);
+            ctx->stats.kernel_launches++;
+        }
         launch_to_float(d_pp, d_ppf, (long long)PP_NF * PIMD_MAXPP * npair, ctx->stream);
     }
     // quartet tiles: for bra pair i of class X and each run of ket pairs of
@@ -752,13 +771,13 @@ struct GemmSet {
 // per-replica GEMM descriptors: C = alpha op(A) op(B) + beta C, square N x N
 // unless K is the occupied count
 static int make_gemm(pimd_ctx* ctx, const char* name, const Batch& bt, const double* A, int ta, const double* B,
-                     int tb, double* C, double alpha, bool kocc, GemmSet& gs)
+                     int tb, double* C, double alpha, bool kocc, GemmSet& gs, double beta = 0.0)
 {
     std::vector<GemmDesc> v(bt.nrep);
     for (int r = 0; r < bt.nrep; r++) {
         const int N = bt.nbf[r];
         const long long o = bt.moff[r];
-        v[r] = GemmDesc{N, N, kocc ? bt.nocc[r] : N, A + o, N, ta, B + o, N, tb, C + o, N, alpha, 0.0, r};
+        v[r] = GemmDesc{N, N, kocc ? bt.nocc[r] : N, A + o, N, ta, B + o, N, tb, C + o, N, alpha, beta, r};
     }
     UPLOAD(name, v, gs.d);
     gs.n = bt.nrep;
@@ -768,6 +787,7 @@ static int make_gemm(pimd_ctx* ctx, const char* name, const Batch& bt, const dou
 
 struct ScfPlan {
     GemmSet FD, FDS, XtE, XtEX, XtF, XtFX, QtF, FQ, QU, XC, Dn, Wn;
+    GemmSet DS, DSD, DSDS, Pur;   // McWeeny step of a reused density in the new overlap metric
 };
 
 static int make_plan(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p)
@@ -786,6 +806,12 @@ static int make_plan(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p)
 
     if ((rc = make_gemm(ctx, "g_Dn", bt, m.C, 0, m.C, 1, m.D, 2.0, true, p.Dn))) return rc;
     if ((rc = make_gemm(ctx, "g_Wn", bt, m.Cs, 0, m.C, 1, m.W, 2.0, true, p.Wn))) return rc;
+    // D <- 3/4 D S D - 1/4 D S D S D (P = D/2: P <- 3 PSP - 2 PSPSP), result in M2
+    if ((rc = make_gemm(ctx, "g_DS", bt, m.D, 0, m.S, 0, m.M1, 1.0, false, p.DS))) return rc;
+    if ((rc = make_gemm(ctx, "g_DSD", bt, m.M1, 0, m.D, 0, m.M2, 0.75, false, p.DSD))) return rc;
+    if ((rc = make_gemm(ctx, "g_DSDS", bt, m.M2, 0, m.S, 0, m.Er, 4.0 / 3.0, false, p.DSDS))) return rc;
+    // (the last product accumulates onto 3/4 DSD already in M2)
+    if ((rc = make_gemm(ctx, "g_Pur", bt, m.Er, 0, m.D, 0, m.M2, -0.25, false, p.Pur, 1.0))) return rc;
     return PIMD_OK;
 }
 
@@ -815,7 +841,8 @@ static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, co
 // G' += G'(M) over all class pairs for the replicas in the active mask, with
 // the quartets screened by Q_ab Q_cd max|M block| >= tau; those below fp32_tau
 // (if > 0) are evaluated in FP32 from Mf, an FP32 copy of M made here
-static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32_tau, const double* M)
+static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32_tau, const double* M,
+                      double tau_prim)
 {
     launch_shell_bounds(bt.S, bt.R, bt.nrep, bt.maxsh, M, bt.Dsh, bt.R.active, ctx->stream);
     ctx->stats.kernel_launches++;
@@ -828,7 +855,7 @@ static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32
     for (int cp = 0; cp < n_class_pairs(); cp++) {
         if (bt.tiles[cp].empty()) continue;
         launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), M, Mf, m.G, ctx->boys, ctx->boysf,
-                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->tile_w[cp], ctx->stream);
+                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->tile_w[cp], tau_prim, ctx->stream);
         ctx->stats.kernel_launches += fp32_tau > tau ? 2 : 1;
     }
     return PIMD_OK;
@@ -935,7 +962,7 @@ static int sad_atomic(pimd_ctx* ctx, const pimd_basis* basis, const std::vector<
     bool conv = false;
     for (int it = 1; it <= 200 && !conv; it++) {
         launch_delta_density(m.rm, n, m.D, m.Dp, m.dD, m.G, d_mode, st);
-        if ((rc = fock_build(ctx, bt, m, 1e-12, 0.0, m.dD))) return rc;
+        if ((rc = fock_build(ctx, bt, m, 1e-12, 0.0, m.dD, 0.0))) return rc;
         launch_fock_assemble(m.rm, n, m.H, m.G, m.F, m.active, st);
         launch_copy_mats(m.rm, n, m.F, m.Fb, nullptr, st);
         if ((rc = density())) return set_err(ctx, rc, "SAD: atom without a 2p shell in the basis");
@@ -1084,7 +1111,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     }
     rc = setup_batch(ctx, bt, nrep, natom_of, Zc, d_xyz, basis, o->schwarz_tau);
     if (rc) return rc;
-    const int hist = std::max(2, std::min(8, o->diis_size));
+    const int hist = std::max(2, std::min(16, o->diis_size));
     Mats m;
     if ((rc = alloc_mats(ctx, bt, m, hist))) return rc;
     ScfPlan plan;
@@ -1135,9 +1162,12 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         core[r] = !use_cache[r] && !learned[r] && !sadm[r];
         nlearned += learned[r];
         nsad += sadm[r];
-        if (use_cache[r])
-            CK(cudaMemcpyAsync(m.C + bt.moff[r], mo.C.p, sizeof(double) * bt.nbf[r] * bt.nbf[r],
-                               cudaMemcpyDeviceToDevice, ctx->stream));
+        if (use_cache[r]) {
+            // the cached MOs, or for reuse_mode 2 the cached Fock matrix (stored with them)
+            const DevBuf& src = o->reuse_mode == 2 ? mo.F : mo.C;
+            CK(cudaMemcpyAsync((o->reuse_mode == 2 ? m.Fb : m.C) + bt.moff[r], src.p,
+                               sizeof(double) * bt.nbf[r] * bt.nbf[r], cudaMemcpyDeviceToDevice, ctx->stream));
+        }
     }
     int* d_mask;
     UPLOAD("mask_core", core, d_mask);
@@ -1149,8 +1179,26 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     // ever multiplied by Jacobi rotations)
     launch_identity(m.rm, nrep, m.Cq, nullptr, ctx->stream);
     launch_copy_mats(m.rm, nrep, m.H, m.Fb, d_mask, ctx->stream);
-    diag_density(ctx, bt, m, plan, d_mask);
-    gemm(ctx, plan.Dn, d_mc);
+    if (o->reuse_mode == 2) {
+        // core-Hamiltonian replicas and reused Fock matrices: one diagonalisation
+        std::vector<int> both(nrep);
+        for (int r = 0; r < nrep; r++) both[r] = core[r] || use_cache[r];
+        int* d_both;
+        UPLOAD("mask_diag0", both, d_both);
+        diag_density(ctx, bt, m, plan, d_both);
+    } else {
+        diag_density(ctx, bt, m, plan, d_mask);
+        gemm(ctx, plan.Dn, d_mc);
+        if (o->reuse_mode == 1)
+            for (int step = 0; step < 2; step++) {
+                gemm(ctx, plan.DS, d_mc);
+                gemm(ctx, plan.DSD, d_mc);
+                gemm(ctx, plan.DSDS, d_mc);
+                gemm(ctx, plan.Pur, d_mc);
+                launch_copy_mats(m.rm, nrep, m.M2, m.D, d_mc, ctx->stream);
+                ctx->stats.kernel_launches++;
+            }
+    }
     if (nlearned > 0) {
         pimd_guess* gm = ctx->guess_model;
         if (guess_device(gm) != ctx->device) return set_err(ctx, PIMD_EINVAL, "guess model on another device");
@@ -1198,7 +1246,7 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         rc = run_seg(ctx, seg_fock, graphs, [&]() -> int {
             launch_delta_density(m.rm, nrep, m.D, m.Dp, m.dD, m.G, d_mode, ctx->stream);
             ctx->stats.kernel_launches++;
-            return fock_build(ctx, bt, m, o->schwarz_tau, o->fp32_tau, m.dD);
+            return fock_build(ctx, bt, m, o->schwarz_tau, o->fp32_tau, m.dD, o->schwarz_tau * o->prim_screen);
         });
         if (rc) return rc;
         CK(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -1311,21 +1359,24 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
         ctx->stats.kernel_launches += 3;
     }
-    // MO cache
+    // MO cache (and the final Fock matrix)
     for (int r = 0; r < nrep; r++) {
         auto& mo = ctx->mo[r];
         const size_t bytes = sizeof(double) * bt.nbf[r] * bt.nbf[r];
-        if (mo.C.cap < bytes) {
-            if (mo.C.p) cudaFree(mo.C.p);
-            mo.C.p = nullptr;
-            mo.C.cap = 0;
-            if (cudaMalloc(&mo.C.p, bytes) != cudaSuccess) {
+        for (DevBuf* b : {&mo.C, &mo.F}) {
+            if (b->cap >= bytes) continue;
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+            b->cap = 0;
+            if (cudaMalloc(&b->p, bytes) != cudaSuccess) {
                 cudaGetLastError();
+                mo.N = 0;
                 return set_err(ctx, PIMD_ENOMEM, "MO cache allocation failed");
             }
-            mo.C.cap = bytes;
+            b->cap = bytes;
         }
         CK(cudaMemcpyAsync(mo.C.p, m.C + bt.moff[r], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(mo.F.p, m.F + bt.moff[r], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         mo.Z.assign(Zc + bt.atom0[r], Zc + bt.atom0[r + 1]);
         mo.N = bt.nbf[r];
     }
@@ -1393,7 +1444,8 @@ static int check_common(pimd_ctx* ctx, const pimd_basis* basis, const pimd_scf_o
         memcpy(&o, opts, opts->struct_size);
     }
     if (!(o.conv_energy > 0) || !(o.conv_error > 0) || o.max_iter < 1 || o.max_iter > 10000 ||
-        !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 5 || o.full_every < 0)
+        !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 5 || o.full_every < 0 || !(o.prim_screen >= 0) ||
+        o.prim_screen > 1.0 || o.reuse_mode < 0 || o.reuse_mode > 2 || o.diis_size > 16)
         return set_err(ctx, PIMD_EINVAL, "bad SCF options");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
     return PIMD_OK;
@@ -1596,7 +1648,8 @@ extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
         rc2 = timed(ms, 4, ci, use, [&](int cp) {
             if (!bt.tiles[cp].empty())
                 launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, Mf, m.G, ctx->boys,
-                          ctx->boysf, o.schwarz_tau, o.fp32_tau, bt.Dsh, bt.cnt + 4 * cp, cand[ci], ctx->stream);
+                          ctx->boysf, o.schwarz_tau, o.fp32_tau, bt.Dsh, bt.cnt + 4 * cp, cand[ci],
+                          o.schwarz_tau * o.prim_screen, ctx->stream);
         });
     }
     double best = 0.0;
@@ -1663,7 +1716,11 @@ extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
     bt.R.active = m.active;
     CK(cudaMemcpyAsync(m.D, D_dev, sizeof(double) * bt.mtot, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemsetAsync(m.G, 0, sizeof(double) * bt.mtot, ctx->stream));
-    if ((rc = fock_build(ctx, bt, m, schwarz_tau, fp32_tau, m.D))) return rc;
+    {
+        pimd_scf_opts d;
+        pimd_scf_opts_default(&d);
+        if ((rc = fock_build(ctx, bt, m, schwarz_tau, fp32_tau, m.D, schwarz_tau * d.prim_screen))) return rc;
+    }
     // G_out = G' + G'^T
     CK(cudaMemsetAsync(m.H, 0, sizeof(double) * bt.mtot, ctx->stream));
     launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, nullptr, ctx->stream);

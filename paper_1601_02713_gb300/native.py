@@ -22,7 +22,7 @@ class PimdScfOpts(ctypes.Structure):
                 ("conv_error", ctypes.c_double), ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int),
                 ("schwarz_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("guess", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("want_gradient", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("full_every", ctypes.c_int)]
+                ("full_every", ctypes.c_int), ("prim_screen", ctypes.c_double), ("reuse_mode", ctypes.c_int)]
 
 
 class PimdInfo(ctypes.Structure):
