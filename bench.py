@@ -11,9 +11,14 @@ memory and reused as the next step's guess).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank runs its own batch of beads on its own GPU (the
-replicas are independent: no collective on the data path, weak scaling); the
-step time is the maximum over ranks.
+Under torchrun the step's replicas are split over the ranks, one GPU each
+(Sec. 2: replica parallelism): beads in equal contiguous blocks, the step
+holding world x (beads per rank) beads (weak scaling); string images, whose
+number is fixed by the workload, in contiguous blocks balanced by their
+screened-quartet counts (strong scaling). After its forces call every rank
+takes part in one all-gather of all replicas' energies and gradients (the
+paper's gather of forces before the replicas move), inside the timed step.
+The step time is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -121,14 +126,21 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- inputs
-def make_steps(name, nrep, nsteps, rank):
+def make_steps(name, nrep, nsteps, world=1):
+    """The job's steps (every rank builds the same sequence): for beads of
+    one molecule, world x nrep beads per step (nrep: beads per rank, default
+    the workload's); string images as the workload defines them."""
     reps, kind = inputs.workload(name, nrep=nrep)
-    if rank and reps.uniform():
-        # each rank has its own beads: re-seed the bead displacements
-        Zb, Xb = reps.Z[0], reps.coords[0] / inputs.ANGSTROM_TO_BOHR
-        reps = inputs.beads(Zb, Xb, len(reps.Z), 10_000 * rank + 17, name)
-    seq = inputs.markov_steps(reps, nsteps, seed=97 + rank)
+    if reps.uniform() and world > 1:
+        reps, kind = inputs.workload(name, nrep=len(reps.Z) * world)
+    seq = inputs.markov_steps(reps, nsteps, seed=97)
     return seq, kind
+
+
+def rank_block(seq, blocks, rank):
+    """This rank's contiguous block of replicas of every step."""
+    s, e = blocks[rank]
+    return [inputs.Replicas(st.Z[s:e], st.coords[s:e], st.name) for st in seq]
 
 
 def max_over_ranks(t_local, dist, device):
@@ -144,7 +156,7 @@ def max_over_ranks(t_local, dist, device):
 
 def job_throughput(beads_per_rank, world, steps, t_max):
     """Whole-job bead evaluations per second: all ranks' beads over the
-    slowest rank's time (weak scaling: each rank owns its own beads)."""
+    slowest rank's time (beads: each rank evaluates its own block of the step)."""
     return beads_per_rank * world * steps / t_max
 
 
@@ -183,7 +195,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    seq, kind = make_steps(args.workload, args.nrep, 1, 0)
+    seq, kind = make_steps(args.workload, args.nrep, 1)
     # SCF iterations per bead evaluation: the mean the GPU path measures on
     # this workload (15.3 for (H2O)8 with MO reuse between steps)
     iters = args.ref_iterations
@@ -220,7 +232,7 @@ def run_guess_study(args):
     B.build()
     from paper_1601_02713_gb300 import native
     torch.cuda.set_device(0)
-    seq, kind = make_steps(args.workload, args.nrep, 2, 0)
+    seq, kind = make_steps(args.workload, args.nrep, 2)
     Z, X0 = seq[0].stacked()
     _, X1 = seq[1].stacked()
     nrep = len(X0)
@@ -309,19 +321,30 @@ def main():
     from paper_1601_02713_gb300 import native
 
     K, W, E2E = args.steps, args.warmup, args.e2e_steps
-    seq, kind = make_steps(args.workload, args.nrep, W + K + E2E, rank)
+    from paper_1601_02713_gb300 import replicas as RP
+    seq_all, kind = make_steps(args.workload, args.nrep, W + K + E2E, world)
+    ragged = not seq_all[0].uniform()
+    ctx = native.Context(local)
+    basis = native.Basis(inputs.basis_set(kind))
+    n_all = len(seq_all[0].Z)
+    atoms_all = [len(z) for z in seq_all[0].Z]
+    if ragged and world > 1:
+        # string images: contiguous blocks balanced by screened-quartet counts
+        nat0, Z0, X0 = seq_all[0].concat()
+        costs = native.pimd_screened_quartets(ctx, basis, nat0, Z0, X0)
+        blocks = RP.balanced_blocks(costs, world)
+    else:
+        blocks = RP.contiguous_blocks(n_all, world)
+    seq = rank_block(seq_all, blocks, rank)
     nrep = len(seq[0].Z)
     # beads of one molecule (pimd_bo_forces) or string images of different
     # sizes (string_images_forces, one ragged batch)
-    ragged = not seq[0].uniform()
     if ragged:
         nat, Z, _ = seq[0].concat()
         natom = int(nat.sum())
     else:
         Z, _ = seq[0].stacked()
         natom = len(Z)
-    ctx = native.Context(local)
-    basis = native.Basis(inputs.basis_set(kind))
     opts = native.scf_opts(guess=1, fp32_tau=args.fp32_tau)
     dev = torch.device("cuda", local)
     X = [torch.tensor(s.concat()[2] if ragged else s.stacked()[1], dtype=torch.float64, device=dev) for s in seq]
@@ -335,13 +358,18 @@ def main():
             dist.barrier()
 
     def step(i):
-        if ragged:
+        if nrep == 0:
+            infos = []
+        elif ragged:
             infos, rc = native.string_images_forces_dev(ctx, basis, nat, Z, X[i], E, G, opts,
                                                         stream=stream.cuda_stream)
         else:
             infos, rc = native.pimd_bo_forces_dev(ctx, basis, Z, X[i], E, G, opts, stream=stream.cuda_stream)
-        if rc != 0:
+        if nrep and rc != 0:
             raise RuntimeError(f"forces call returned {rc}")
+        if dist is not None:
+            # every rank gets every replica's energy and gradient (one all-gather)
+            RP.gather_results(E, G, blocks, atoms_all, dist, dev)
         return infos
 
     # autotuner (not timed): kernel variants for this workload (replicas of
@@ -369,13 +397,15 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms.append(e0.elapsed_time(e1))
-        stats.append(native.pimd_last_stats(ctx))
-        iters.append(float(np.mean([x["iterations"] for x in infos])))
+        if nrep:
+            stats.append(native.pimd_last_stats(ctx))
+            iters.append(float(np.mean([x["iterations"] for x in infos])))
         assert all(x["converged"] for x in infos)
     clk = clocks.stop()
     t_local = sum(ms) / 1000.0
     t_max = max_over_ranks(t_local, dist, dev)
-    value = job_throughput(nrep, world, K, t_max)
+    # whole job: every replica of the step (all ranks' blocks) per step
+    value = n_all * K / t_max
 
     # end to end through the host-buffer entry point (H2D coords, D2H E and G)
     # the step inputs in pinned host memory (the H2D copy is part of the call)
@@ -388,16 +418,21 @@ def main():
     barrier()
     t0 = time.perf_counter()
     for x in Xh:
-        if ragged:
+        if nrep == 0:
+            Eh, Gh = np.zeros(0), np.zeros((0, 3))
+        elif ragged:
             Eh, Gh, info_h, rc = native.string_images_forces(ctx, basis, nat, Z, x, opts)
+            assert rc == 0
         else:
             Eh, Gh, info_h, rc = native.pimd_bo_forces(ctx, basis, Z, x, opts)
-        assert rc == 0
+            assert rc == 0
+        if dist is not None:
+            RP.gather_results(Eh, Gh, blocks, atoms_all, dist, dev)
     t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
-    e2e_value = job_throughput(nrep, world, E2E, t_e2e)
+    e2e_value = n_all * E2E / t_e2e
 
     # roofline of the dominant kernel (the Fock build: all quartet classes)
-    fock_ms = sum(s["ms_fock"] for s in stats)
+    fock_ms = max(sum(s["ms_fock"] for s in stats), 1e-9)
     builds = sum(s["fock_builds"] for s in stats)
     flops = sum(s["eri_flops_per_build"] * s["fock_builds"] for s in stats)
     flops32 = sum(s["eri_flops32_per_build"] * s["fock_builds"] for s in stats)
@@ -416,9 +451,11 @@ def main():
         basis_txt = f"{kind} (even-tempered, {Bq.nbf(Z)} functions)"
         coord_bytes = nrep * natom * 3 * 8
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True,
+            "scaling": "strong" if ragged else "weak", "vs_baseline": None,
             "dtype": "f64" if args.fp32_tau == 0 else "f64+f32", "data": "synthetic",
-            "config": {"workload": args.workload, "beads_per_rank": nrep,
+            "config": {"workload": args.workload, "beads_per_rank": nrep, "replicas_per_step": n_all,
+                       "rank_blocks": blocks,
                        "atoms": natom if not ragged else f"{min(len(z) for z in seq[0].Z)}-"
                                                          f"{max(len(z) for z in seq[0].Z)} per image",
                        "basis": basis_txt,
@@ -436,7 +473,7 @@ def main():
             "ms_split_per_step": {"fock": fock_ms / K, "grad2e": sum(s["ms_grad2e"] for s in stats) / K,
                                   "other": (t_local * 1000.0 - fock_ms - sum(s["ms_grad2e"] for s in stats)) / K},
             "eri_flops32_per_step": sum(s["eri_flops32_per_build"] * s["fock_builds"] for s in stats) / K,
-            "scf_iterations_mean": statistics.mean(iters),
+            "scf_iterations_mean": statistics.mean(iters) if iters else None,
             "roofline": {"kernel": "jk_kernel (one Fock build = all quartet classes)", "bound": "alu",
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,

@@ -149,6 +149,16 @@ int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* natom_of_img, c
                              const double* coords_concat_dev, const pimd_basis* basis, const pimd_scf_opts* opts,
                              double* energies_dev, double* gradients_concat_dev, pimd_info* info, void* stream);
 
+/* Screening stage alone (Schwarz factors and quartet lists, Sec. 3.1 cutoff):
+ * counts[r] = shell quartets of replica r whose bound Q_ab Q_cd is at least
+ * schwarz_tau, for nrep replicas laid out as in string_images_forces (host
+ * arrays). The work of a replica's Fock build grows with this count; a caller
+ * that splits one step's replicas over several GPUs balances the parts by it
+ * (the paper's load balance over images, Sec. 3.2). */
+int pimd_screened_quartets(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Z_concat,
+                           const double* coords_concat, const pimd_basis* basis, double schwarz_tau,
+                           long long* counts);
+
 /* Drop the cached MOs (guesses 1, 3 and 5 then start from their fallback:
  * the core Hamiltonian, the learned density, SAD). */
 void pimd_ctx_clear_guess(pimd_ctx* ctx);

@@ -1544,6 +1544,31 @@ extern "C" int string_images_forces(pimd_ctx* ctx, int nimg, const int* natom_of
                        gradients_concat, false, info, nullptr);
 }
 
+extern "C" int pimd_screened_quartets(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc,
+                                      const double* coords, const pimd_basis* basis, double schwarz_tau,
+                                      long long* counts)
+{
+    if (!ctx || !basis || nrep <= 0 || !natom_of || !Zc || !coords || !counts || !(schwarz_tau >= 0))
+        return PIMD_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
+    long long natot = 0;
+    for (int r = 0; r < nrep; r++) {
+        if (natom_of[r] <= 0 || natom_of[r] > 100000) return set_err(ctx, PIMD_EINVAL, "bad atom count");
+        natot += natom_of[r];
+    }
+    for (long long i = 0; i < natot * 3; i++)
+        if (!isfinite(coords[i])) return set_err(ctx, PIMD_EINVAL, "non-finite coordinates");
+    double* d_xyz;
+    ENSURE("xyz", natot * 3, d_xyz);
+    CK(cudaMemcpyAsync(d_xyz, coords, sizeof(double) * natot * 3, cudaMemcpyHostToDevice, ctx->stream));
+    Batch bt;
+    bt.allow_odd = true;
+    const int rc = setup_batch(ctx, bt, nrep, natom_of, Zc, d_xyz, basis, schwarz_tau);
+    if (rc) return rc;
+    for (int r = 0; r < nrep; r++) counts[r] = bt.nquart_rep[r];
+    return PIMD_OK;
+}
+
 extern "C" int pimd_bo_forces_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double* coords_dev,
                                   const pimd_basis* basis, const pimd_scf_opts* opts, double* energies_dev,
                                   double* gradients_dev, pimd_info* info, void* stream)

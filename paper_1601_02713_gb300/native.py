@@ -80,6 +80,8 @@ def load(path: str | None = None):
     lib.string_images_forces_dev.argtypes = [_P, ctypes.c_int, _I, _I, _P, _P, ctypes.POINTER(PimdScfOpts), _P, _P,
                                              ctypes.POINTER(PimdInfo), _P]
     lib.pimd_last_stats.argtypes = [_P, ctypes.POINTER(PimdStats)]
+    lib.pimd_screened_quartets.argtypes = [_P, ctypes.c_int, _I, _I, _D, _P, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_longlong)]
     lib.pimd_last_trace.argtypes = [_P, ctypes.c_int, ctypes.c_int, _D, _D, _I]
     lib.pimd_fock_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.c_double, ctypes.c_double, _P, _P]
     lib.pimd_one_electron.argtypes = [_P, ctypes.c_int, _I, _D, _P, _D, _D, _D]
@@ -326,6 +328,20 @@ def pimd_bf16_gemm_dev(A, B, C, ta: bool, tb: bool, stream: int = 0) -> int:
     K = int(A.shape[0] if ta else A.shape[1])
     return load().pimd_bf16_gemm_dev(M, N, K, _P(A.data_ptr()), int(A.stride(0)), int(ta), _P(B.data_ptr()),
                                      int(B.stride(0)), int(tb), _P(C.data_ptr()), int(C.stride(0)), _P(stream))
+
+
+def pimd_screened_quartets(ctx: Context, basis: Basis, natom_of_img, Z_concat, coords_concat,
+                           schwarz_tau: float = 1e-12) -> np.ndarray:
+    """Screened shell quartets per replica (host arrays, layout of
+    string_images_forces)."""
+    nat = np.ascontiguousarray(natom_of_img, np.int32)
+    Z = np.ascontiguousarray(Z_concat, np.int32)
+    X = np.ascontiguousarray(coords_concat, np.float64)
+    out = np.zeros(len(nat), np.int64)
+    _check(load().pimd_screened_quartets(ctx.handle, len(nat), _ip(nat), _ip(Z), _dp(X), basis.handle,
+                                         float(schwarz_tau), out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))),
+           "pimd_screened_quartets")
+    return out
 
 
 def pimd_last_trace(ctx: Context, rep: int) -> dict:
