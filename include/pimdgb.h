@@ -80,7 +80,11 @@ typedef struct {
     double prim_screen;   /* 1/81: within a screened shell quartet, primitive quartets whose bound
                              qp_ij qp_kl max|D block| (qp: Schwarz factor of one primitive pair) is
                              below schwarz_tau * prim_screen are skipped in the Fock build (at most
-                             81 per quartet, so their sum stays below schwarz_tau); 0 keeps all */
+                             81 per quartet, so their sum stays below schwarz_tau); in the gradient,
+                             whose quartets are screened at schwarz_tau / 100 on Q_ab Q_cd |Gamma|, a
+                             primitive quartet is skipped below schwarz_tau / 100 * prim_screen with
+                             the derivative-scaled bound (qg_ij qp_kl + qp_ij qg_kl) |Gamma|, qg =
+                             qp 2 sqrt(2 max exponent); 0 keeps all */
     int reuse_mode;       /* start of a replica from its previous call (guess 1, 3, 5): 0 the density
                              2 C_occ C_occ^T of the cached MOs; 1 that density after two McWeeny
                              purification steps in the new overlap metric; 2 the aufbau density of

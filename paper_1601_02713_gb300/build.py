@@ -167,9 +167,9 @@ def generate_sources():
                   f"    if (n > 0) schwarz_kernel<Cls_{nm}><<<(n + 127) / 128, 128, 0, st>>>(P, S, list, n, boys, Q);",
                   "}",
                   f"void launch_prim_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
-                  "                               const double* boys, double* pp, float* qp, cudaStream_t st)",
+                  "                               const double* boys, double* pp, float* qp, float* qg, cudaStream_t st)",
                   "{",
-                  f"    if (n > 0) prim_schwarz_kernel<Cls_{nm}><<<(n + 127) / 128, 128, 0, st>>>(P, S, list, n, boys, pp, qp);",
+                  f"    if (n > 0) prim_schwarz_kernel<Cls_{nm}><<<(n + 127) / 128, 128, 0, st>>>(P, S, list, n, boys, pp, qp, qg);",
                   "}"]
         e.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_eri_{nm}.cu")
@@ -188,7 +188,7 @@ def generate_sources():
         gl += [f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                "                        const double* D, double* grad, const double* boys, const float* boysf,",
                "                        double tau, double fp32_tau, const double* Dsh, int variant, int bs,",
-               "                        cudaStream_t st)",
+               "                        double tp, cudaStream_t st)",
                "{",
                "    if (ntiles <= 0) return;",
                "    const double split = fp32_tau > tau ? fp32_tau : tau;"]
@@ -197,18 +197,19 @@ def generate_sources():
                    "        CoopTape t; int W, Wf; size_t bytes, bytesf;",
                    f"        coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
                    f"        grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R,",
-                   "            tiles, D, grad, boys, split, 1e300, Dsh, t);",
+                   "            tiles, D, grad, boys, split, 1e300, Dsh, t, tp);",
                    "        if (fp32_tau > tau)",
                    f"            grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S,",
-                   "                R, tiles, D, grad, boysf, tau, fp32_tau, Dsh, t);",
+                   "                R, tiles, D, grad, boysf, tau, fp32_tau, Dsh, t, tp);",
                    "        return;",
                    "    }"]
         if not heavy[nm]:
             gl += ["    const int b = bs > 0 ? bs : 128;",
-                   f"    grad2e_kernel<GCls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boys, split, 1e300, Dsh);",
+                   f"    grad2e_kernel<GCls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boys, split, 1e300, Dsh,",
+                   "                                                            tp);",
                    "    if (fp32_tau > tau)",
                    f"        grad2e_kernel<GCls_{nm}, float><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boysf, tau, fp32_tau,",
-                   "                                                           Dsh);"]
+                   "                                                           Dsh, tp);"]
         gl.append("}")
         gl.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_grad_{nm}.cu")
@@ -220,9 +221,9 @@ def generate_sources():
               "const double*, const float*, double, double, const double*, unsigned long long*, int, double, "
               "cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
-    sig_psw = "const Pairs&, const Shells&, const int*, int, const double*, double*, float*, cudaStream_t"
+    sig_psw = "const Pairs&, const Shells&, const int*, int, const double*, double*, float*, float*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-             "const float*, double, double, const double*, int, int, cudaStream_t")
+             "const float*, double, double, const double*, int, int, double, cudaStream_t")
     for c, nm in zip(classes, names):
         d.append(f"void launch_jk_{nm}({sig_jk});")
         if (c[0], c[1]) == (c[2], c[3]):
@@ -269,15 +270,15 @@ def generate_sources():
     d.append(f"typedef void (*PswFn)({sig_psw});")
     d.append("static const PswFn psw_tab[] = {" + ", ".join(f"launch_prim_schwarz_{nm}" for nm in same) + "};")
     d.append("void launch_prim_schwarz(int X, const Pairs& P, const Shells& S, const int* list, int n, "
-             "const double* boys, double* pp, float* qp, cudaStream_t st)")
-    d.append("{ psw_tab[X](P, S, list, n, boys, pp, qp, st); }")
+             "const double* boys, double* pp, float* qp, float* qg, cudaStream_t st)")
+    d.append("{ psw_tab[X](P, S, list, n, boys, pp, qp, qg, st); }")
     d.append(f"typedef void (*GFn)({sig_g});")
     d.append("static const GFn g_tab[] = {" + ", ".join(f"launch_grad2e_{nm}" for nm in names) + "};")
 
     d.append("void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, double* grad, const double* boys, const float* boysf, double tau, double fp32_tau, "
-             "const double* Dsh, int variant, int bs, cudaStream_t st)")
-    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, variant, bs, st); }")
+             "const double* Dsh, int variant, int bs, double tau_prim, cudaStream_t st)")
+    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, variant, bs, tau_prim, st); }")
     d.append("void grad2e_tapes_upload() {")
     for nm in names:
         d.append(f"    grad2e_upload_{nm}();")

@@ -16,10 +16,10 @@
 namespace pimd {
 
 struct CoopTape {
-    const int* vrr;        // 8 ints per op, level-sorted
+    const int* vrr;        // 4 ints per op (see coop_vrr), level-sorted, each level by chain length
     const int* vrr_lv;     // level offsets
     const int* acc;        // 4 ints per op: dst, src, weight, 0
-    const int* hrr[6];     // HRR tapes (energy: [0] only; gradient: Ap Bp Cp Am Bm Cm)
+    const int* hrr[6];     // HRR tapes, 2 ints per op (energy: [0] only; gradient: Ap Bp Cp Am Bm Cm)
     const int* hrr_lv[6];
     const int* out[6];     // slots of the Cartesian outputs of each HRR tape
     int nvlev, naccop, nhlev[6], nhrr;
@@ -38,51 +38,63 @@ __device__ __forceinline__ R warp_sum_r(R v)
 // per primitive quartet in shared memory: PA, WP, QC, WQ (12), o2p, o2pr, o2q,
 // o2qr, o2pq (5), 2a, 2b, 2c (3), then F_m * theta (L + 1)
 constexpr int COOP_NG0 = 20;
+// coefficient table of the primitive quartet being recursed: PA, WP, QC, WQ
+// (0..11), then k o2p, -k o2pr, k o2q, -k o2qr, k o2pq for k = 1..5 (12..36)
+constexpr int COOP_CT = 37;
+constexpr int COOP_KMAX = 5;
 
+// coefficient table ct of one primitive from its geometry g (lane-parallel)
 template <typename R>
-__device__ __forceinline__ R sel3(int d, const R* v) { return d == 0 ? v[0] : (d == 1 ? v[1] : v[2]); }
-
-// run the level-sorted VRR of one primitive quartet (geometry g) in sm
-template <typename R>
-__device__ __forceinline__ void coop_vrr(const CoopTape& tp, R* sm, const R* g, int lane)
+__device__ __forceinline__ void coop_fill_ct(const R* g, R* ct, int lane)
 {
-    R PA[3] = {g[0], g[1], g[2]}, WP[3] = {g[3], g[4], g[5]}, QC[3] = {g[6], g[7], g[8]},
-      WQ[3] = {g[9], g[10], g[11]};
-    const R o2p = g[12], o2pr = g[13], o2q = g[14], o2qr = g[15], o2pq = g[16];
+    if (lane < 12) {
+        ct[lane] = g[lane];
+    } else if (lane < COOP_CT) {
+        const int t = (lane - 12) / COOP_KMAX, k = (lane - 12) % COOP_KMAX + 1;
+        const R v = R(k) * g[12 + t];
+        ct[lane] = (t == 1 || t == 3) ? -v : v;
+    }
+}
+
+// run the level-sorted VRR of one primitive quartet (coefficients ct) in sm:
+// every op is sm[dst] = sum over its 2..5 terms of ct[c_t] sm[s_t], encoded
+// as {dst | s1 << 16, s2 | s3 << 16, s4 | s5 << 16, c1 | c2 << 6 | c3 << 12 |
+// c4 << 18 | c5 << 24 | (terms - 2) << 30}
+template <typename R>
+__device__ __forceinline__ void coop_vrr(const CoopTape& tp, R* sm, const R* ct, int lane)
+{
     for (int lv = 0; lv < tp.nvlev; lv++) {
         const int hi = __ldg(tp.vrr_lv + lv + 1);
         for (int o = __ldg(tp.vrr_lv + lv) + lane; o < hi; o += 32) {
-            const int4 a = __ldg((const int4*)(tp.vrr + 8 * o));
-            const int4 b = __ldg((const int4*)(tp.vrr + 8 * o + 4));
-            // a = {kind, dst, s1, s2}, b = {s3, s4, s5, aux}
-            const int dir = b.w & 15, k1 = (b.w >> 4) & 15, k2 = b.w >> 8;
-            R v;
-            if (a.x == 0) {
-                v = sel3(dir, PA) * sm[a.z] + sel3(dir, WP) * sm[a.w];
-                if (b.x >= 0) v += k1 * (o2p * sm[b.x] - o2pr * sm[b.y]);
-            } else {
-                v = sel3(dir, QC) * sm[a.z] + sel3(dir, WQ) * sm[a.w];
-                if (b.x >= 0) v += k1 * (o2q * sm[b.x] - o2qr * sm[b.y]);
-                if (b.z >= 0) v += k2 * o2pq * sm[b.z];
-            }
-            sm[a.y] = v;
+            const int4 op = __ldg((const int4*)(tp.vrr + 4 * o));
+            const unsigned w0 = (unsigned)op.x, w1 = (unsigned)op.y, w2 = (unsigned)op.z, w3 = (unsigned)op.w;
+            const unsigned n = w3 >> 30;
+            R v = ct[w3 & 63] * sm[w0 >> 16];
+            v = fma(ct[(w3 >> 6) & 63], sm[w1 & 0xffff], v);
+            if (n >= 1) v = fma(ct[(w3 >> 12) & 63], sm[w1 >> 16], v);
+            if (n >= 2) v = fma(ct[(w3 >> 18) & 63], sm[w2 & 0xffff], v);
+            if (n >= 3) v = fma(ct[(w3 >> 24) & 63], sm[w2 >> 16], v);
+            sm[w0 & 0xffff] = v;
         }
         __syncwarp();
     }
 }
 
+// HRR op {dst | s1 << 16, s2 | c << 16}: sm[dst] = sm[s1] + hc[c] sm[s2],
+// hc = (AB_x, AB_y, AB_z, CD_x, CD_y, CD_z)
 template <typename R>
-__device__ __forceinline__ void coop_hrr(const CoopTape& tp, int h, R* sm, const R AB[3], const R CD[3], int lane)
+__device__ __forceinline__ void coop_hrr(const CoopTape& tp, int h, R* sm, const R hc[6], int lane)
 {
     const int* ops = tp.hrr[h];
     const int* lvo = tp.hrr_lv[h];
     for (int lv = 0; lv < tp.nhlev[h]; lv++) {
         const int hi = __ldg(lvo + lv + 1);
         for (int o = __ldg(lvo + lv) + lane; o < hi; o += 32) {
-            const int4 a = __ldg((const int4*)(ops + 8 * o));
-            const int dir = __ldg(ops + 8 * o + 7);
-            const R c = a.x == 3 ? sel3(dir, AB) : sel3(dir, CD);
-            sm[a.y] = sm[a.z] + c * sm[a.w];
+            const int2 op = __ldg((const int2*)(ops + 2 * o));
+            const unsigned a = (unsigned)op.x, b = (unsigned)op.y;
+            const unsigned c = b >> 16;
+            const R coef = c == 0 ? hc[0] : c == 1 ? hc[1] : c == 2 ? hc[2] : c == 3 ? hc[3] : c == 4 ? hc[4] : hc[5];
+            sm[a & 0xffff] = fma(coef, sm[b & 0xffff], sm[a >> 16]);
         }
         __syncwarp();
     }
@@ -119,12 +131,14 @@ __device__ __forceinline__ void coop_prim(const Pairs& P, int ab, int cd, int k,
 }
 
 // contracted accumulators of one quartet: zero, then every primitive quartet
-// through the VRR and the accumulation ops. Primitive quartets (i|j) with
-// qp_i qp_j < qthr are skipped (qthr <= 0: none); returns the number evaluated.
+// through the VRR and the accumulation ops. Primitive quartets (i|j) whose
+// bound is below qthr are skipped (qthr <= 0: none): qp_i qp_j for the Fock
+// build, qg_i qp_j + qp_i qg_j for the gradient (grad); returns the number
+// evaluated.
 template <typename R>
 __device__ __forceinline__ int coop_primitive_loop(const CoopTape& tp, const Pairs& P, int ab, int cd,
-                                                   const R* __restrict__ boys, R* sm, R* geom, int lane,
-                                                   float qthr = 0.0f)
+                                                   const R* __restrict__ boys, R* sm, R* geom, R* ct, int lane,
+                                                   float qthr = 0.0f, bool grad = false)
 {
     const int NG = COOP_NG0 + tp.L + 1;
     for (int i = lane; i < tp.NACC; i += 32) sm[i] = R(0);
@@ -133,8 +147,11 @@ __device__ __forceinline__ int coop_primitive_loop(const CoopTape& tp, const Pai
     for (int base = 0; base < npq; base += 32) {
         const int k = base + lane;
         bool keep = k < npq;
-        if (keep && qthr > 0.0f)
-            keep = __ldg(P.qp + (size_t)(k % nab) * P.n + ab) * __ldg(P.qp + (size_t)(k / nab) * P.n + cd) >= qthr;
+        if (keep && qthr > 0.0f) {
+            const size_t i = (size_t)(k % nab) * P.n + ab, j = (size_t)(k / nab) * P.n + cd;
+            keep = grad ? __ldg(P.qg + i) * __ldg(P.qp + j) + __ldg(P.qp + i) * __ldg(P.qg + j) >= qthr
+                        : __ldg(P.qp + i) * __ldg(P.qp + j) >= qthr;
+        }
         const unsigned mask = __ballot_sync(0xffffffffu, keep);
         if (keep) coop_prim<R>(P, ab, cd, k, nab, tp.L, boys, geom + __popc(mask & ((1u << lane) - 1u)) * NG);
         __syncwarp();
@@ -143,8 +160,9 @@ __device__ __forceinline__ int coop_primitive_loop(const CoopTape& tp, const Pai
         for (int p = 0; p < nb; p++) {
             const R* g = geom + p * NG;
             if (lane <= tp.L) sm[tp.F0 + lane] = g[COOP_NG0 + lane];
+            coop_fill_ct<R>(g, ct, lane);
             __syncwarp();
-            coop_vrr<R>(tp, sm, g, lane);
+            coop_vrr<R>(tp, sm, ct, lane);
             const R w[4] = {R(1), g[17], g[18], g[19]};
             for (int o = lane; o < tp.naccop; o += 32) {
                 const int4 a = __ldg((const int4*)(tp.acc + 4 * o));
@@ -270,7 +288,7 @@ __device__ __forceinline__ void coop_scatter_jk(const R* I, double f, int fa, in
 // shared memory (elements) of one warp
 __host__ __device__ constexpr int coop_warp_doubles(int NACC, int NWORK, int L, int ncart4)
 {
-    return NACC + NWORK + 32 * (COOP_NG0 + L + 1) + 2 * ncart4;
+    return NACC + NWORK + 32 * (COOP_NG0 + L + 1) + 2 * ncart4 + COOP_CT;
 }
 
 // Fock build of the quartets whose density-weighted bound lies in [tau_lo, tau_hi)
@@ -291,6 +309,7 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
     Rt* geom = sm + tp.NACC + tp.NWORK;
     Rt* cart = geom + 32 * (COOP_NG0 + tp.L + 1);
     Rt* tmp = cart + NC4;
+    Rt* ct = tmp + NC4;
     const Tile t = tiles[blockIdx.x];
     if (!R.active[t.rep]) return;
     const int ab = t.ab, r = t.rep;
@@ -312,14 +331,14 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        const int nprim = coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, lane, (float)(tau_prim / dq));
+        const int nprim = coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, ct, lane, (float)(tau_prim / dq));
         if (lane == 0) {
             atomicAdd(cnt, 1ull);
             atomicAdd(cnt + 1, (unsigned long long)nprim);
         }
-        const Rt AB[3] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2])};
-        const Rt CD[3] = {Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
-        coop_hrr<Rt>(tp, 0, sm, AB, CD, lane);
+        const Rt hc[6] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2]),
+                          Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
+        coop_hrr<Rt>(tp, 0, sm, hc, lane);
         for (int e = lane; e < NC4; e += 32) cart[e] = sm[__ldg(tp.out[0] + e)];
         __syncwarp();
         coop_cart_to_sph<LA, LB, LC, LD, Rt>(cart, tmp, lane);
@@ -341,7 +360,8 @@ template <int LA, int LB, int LC, int LD, typename Rt>
 __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
                                                           const double* __restrict__ Dall, double* __restrict__ grad,
                                                           const Rt* __restrict__ boys, double tau_lo, double tau_hi,
-                                                          const double* __restrict__ Dsh, CoopTape tp)
+                                                          const double* __restrict__ Dsh, CoopTape tp,
+                                                          double tau_prim)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Rt* smem = (Rt*)smem_raw;
@@ -353,6 +373,7 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
     Rt* geom = sm + tp.NACC + tp.NWORK;
     Rt* gc = geom + 32 * (COOP_NG0 + tp.L + 1);
     Rt* tmp = gc + NC4;
+    Rt* ct = tmp + NC4;
     const Tile t = tiles[blockIdx.x];
     const int ab = t.ab, r = t.rep;
     const int sa = P.sa[ab], sb = P.sb[ab];
@@ -365,14 +386,15 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
     const double* D = Dall + R.moff[r];
     for (int cd = t.c0 + w; cd < t.c1; cd += W) {
         const int sc = P.sa[cd], sd = P.sb[cd];
-        const double bound = P.Q[ab] * P.Q[cd] * gamma_bound(R, Dsh, r, sa, sb, sc, sd);
+        const double gam = gamma_bound(R, Dsh, r, sa, sb, sc, sd);
+        const double bound = P.Q[ab] * P.Q[cd] * gam;
         if (bound < tau_lo || bound >= tau_hi) continue;
         double Cc[3], Dd[3];
         for (int x = 0; x < 3; x++) {
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, lane);
+        coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, ct, lane, (float)(tau_prim / gam), true);
         // Gamma: spherical, then the transpose transform to Cartesian components
         double f = 1.0;
         if (sa == sb) f *= 0.5;
@@ -391,12 +413,12 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
             __syncwarp();
             coop_sph_to_cart_t<LA, LB, LC, LD, Rt>(gc, tmp, lane);
         }
-        const Rt AB[3] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2])};
-        const Rt CD[3] = {Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
+        const Rt hc[6] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2]),
+                          Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
         Rt gX[3][3] = {{Rt(0), Rt(0), Rt(0)}, {Rt(0), Rt(0), Rt(0)}, {Rt(0), Rt(0), Rt(0)}};
         // tapes in the order Ap, Bp, Cp, then the lowered ones that exist
         for (int h = 0; h < tp.nhrr; h++) {
-            coop_hrr<Rt>(tp, h, sm, AB, CD, lane);
+            coop_hrr<Rt>(tp, h, sm, hc, lane);
             const int pos = tp.hpos[h];
             const bool up = tp.hup[h] != 0;
             const int lp = Ls[pos] + (up ? 1 : -1);

@@ -464,7 +464,8 @@ __global__ void __launch_bounds__(128) schwarz_kernel(Pairs P, Shells S, const i
 // in place) and qp is stored in that order.
 template <class C>
 __global__ void __launch_bounds__(128) prim_schwarz_kernel(Pairs P, Shells S, const int* __restrict__ list, int n,
-                                                           const double* __restrict__ boys, double* pp, float* qp)
+                                                           const double* __restrict__ boys, double* pp, float* qp,
+                                                           float* qg)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
@@ -519,7 +520,16 @@ __global__ void __launch_bounds__(128) prim_schwarz_kernel(Pairs P, Shells S, co
         for (int k = 0; k < np; k++) v[k] = pp[((size_t)f * PIMD_MAXPP + k) * N + ab];
         for (int k = 0; k < np; k++) pp[((size_t)f * PIMD_MAXPP + k) * N + ab] = v[perm[k]];
     }
-    for (int k = 0; k < PIMD_MAXPP; k++) qp[(size_t)k * N + ab] = k < np ? q[perm[k]] : 0.0f;
+    for (int k = 0; k < PIMD_MAXPP; k++) {
+        float g = 0.0f;
+        if (k < np) {
+            const double ea = pp[((size_t)PP_EA * PIMD_MAXPP + k) * N + ab];
+            const double eb = pp[((size_t)PP_EB * PIMD_MAXPP + k) * N + ab];
+            g = q[perm[k]] * __double2float_ru(2.0 * sqrt(2.0 * fmax(ea, eb)));
+        }
+        qp[(size_t)k * N + ab] = k < np ? q[perm[k]] : 0.0f;
+        qg[(size_t)k * N + ab] = g;
+    }
 }
 
 }  // namespace pimd

@@ -448,12 +448,70 @@ HRR_NAMES = ["Ap", "Bp", "Cp", "Am", "Bm", "Cm"]
 # Level-scheduled tapes for the warp-cooperative kernels of the largest
 # classes: every intermediate lives in shared memory and the ops of one
 # dependency level are independent, so the 32 lanes of a warp execute a level
-# in parallel. Slot layout: [0, NACC) accumulators, then F_m at F0 .. F0+L,
-# then VRR intermediates; the HRR intermediates reuse the space from F0 on.
-# Op = 8 ints {kind, dst, s1, s2, s3, s4, s5, aux}:
-#   kind 0/1: bra/ket VRR (aux = dir | k1 << 4 | k2 << 8), kind 3/4: bra/ket HRR
-#   (aux = dir); accumulation op = 4 ints {dst, src, weight, 0}.
+# in parallel, with a __syncwarp between levels. Slot layout: [0, NACC)
+# accumulators, then F_m at F0 .. F0+L, then VRR intermediates; the HRR
+# intermediates reuse the space from F0 on.
+# Generator-side op = {kind, dst, s1, s2, s3, s4, s5, aux}: kind 0/1 bra/ket
+# VRR (aux = dir | k1 << 4 | k2 << 8), kind 3/4 bra/ket HRR (aux = dir).
+# Emitted forms (see coop_kernels.cuh):
+#   VRR op = 4 ints, one fused multiply-add chain sum_t ct[c_t] sm[s_t] over
+#     2..5 terms, ct = the primitive quartet's coefficient table (COOP_CT
+#     entries); the ops of a level are sorted by their number of terms;
+#   HRR op = 2 ints {dst | s1 << 16, s2 | coef << 16}: sm[dst] = sm[s1] +
+#     hc[coef] sm[s2], hc = (AB_x, AB_y, AB_z, CD_x, CD_y, CD_z);
+#   accumulation op = 4 ints {dst, src, weight, 0}.
 # ---------------------------------------------------------------------------
+# coefficient table of one primitive quartet: PA, WP, QC, WQ (0..11), then
+# k o2p, -k o2pr, k o2q, -k o2qr, k o2pq for k = 1..5 (12..36)
+COOP_KMAX = 5
+CT_PA, CT_WP, CT_QC, CT_WQ = 0, 3, 6, 9
+CT_O2P, CT_O2PR, CT_O2Q, CT_O2QR, CT_O2PQ = 12, 17, 22, 27, 32
+COOP_CT = 37
+
+
+def _i32(x):
+    return x - (1 << 32) if x >= (1 << 31) else x
+
+
+def encode_vrr(op):
+    """(nterms, 4-int word) of one VRR op as a chain of products."""
+    kind, d, s1, s2, s3, s4, s5, aux = op
+    i, k1, k2 = aux & 15, (aux >> 4) & 15, aux >> 8
+    assert k1 <= COOP_KMAX and k2 <= COOP_KMAX and max(d, s1, s2, s3, s4, s5) < 65536
+    if kind == 0:
+        terms = [(CT_PA + i, s1), (CT_WP + i, s2)]
+        if s3 >= 0:
+            terms += [(CT_O2P + k1 - 1, s3), (CT_O2PR + k1 - 1, s4)]
+    else:
+        terms = [(CT_QC + i, s1), (CT_WQ + i, s2)]
+        if s3 >= 0:
+            terms += [(CT_O2Q + k1 - 1, s3), (CT_O2QR + k1 - 1, s4)]
+        if s5 >= 0:
+            terms += [(CT_O2PQ + k2 - 1, s5)]
+    n = len(terms)
+    cs = [t[0] for t in terms] + [0] * (5 - n)
+    ss = [t[1] for t in terms] + [0] * (5 - n)
+    w = (d | (ss[0] << 16), ss[1] | (ss[2] << 16), ss[3] | (ss[4] << 16),
+         cs[0] | (cs[1] << 6) | (cs[2] << 12) | (cs[3] << 18) | (cs[4] << 24) | ((n - 2) << 30))
+    return n, [_i32(x) for x in w]
+
+
+def encode_vrr_levels(ops, lv):
+    """Encoded ops, each level's ops sorted by term count (a warp's round of
+    32 ops then mostly runs one chain length)."""
+    out = []
+    for a in range(len(lv) - 1):
+        enc = sorted((encode_vrr(op) for op in ops[lv[a]:lv[a + 1]]), key=lambda t: t[0])
+        out += [w for _, w in enc]
+    return out
+
+
+def encode_hrr(op):
+    kind, d, s1, s2, _, _, _, i = op
+    assert max(d, s1, s2) < 65536
+    return [_i32(d | (s1 << 16)), s2 | ((i if kind == 3 else 3 + i) << 16)]
+
+
 # a class gets a cooperative tape above these VRR sizes (lines); its
 # straight-line kernel is generated up to the MAX sizes; where both exist the
 # autotuner picks one per class. For the Fock build the cooperative kernel is
@@ -604,12 +662,12 @@ def coop_header(nm, grad, t):
 
     out = [f"// Generated by gen_eri.py: level-scheduled {'gradient' if grad else 'Fock'} tape of class {nm}.\n",
            "#pragma once\n\n"]
-    out.append(arr(f"{pre}_vrr", [x for op in t["vrr"] for x in op]))
+    out.append(arr(f"{pre}_vrr", [x for w in encode_vrr_levels(t["vrr"], t["vrr_lv"]) for x in w]))
     out.append(arr(f"{pre}_vrr_lv", t["vrr_lv"]))
     out.append(arr(f"{pre}_acc", [x for op in t["acc"] for x in op]))
     names = []
     for hname, sops, slv, outs in t["hrrs"]:
-        out.append(arr(f"{pre}_hrr{hname}", [x for op in sops for x in op]))
+        out.append(arr(f"{pre}_hrr{hname}", [x for op in sops for x in encode_hrr(op)]))
         out.append(arr(f"{pre}_hrr{hname}_lv", slv))
         out.append(arr(f"{pre}_out{hname}", outs))
         names.append((hname, len(sops), len(slv) - 1, len(outs)))

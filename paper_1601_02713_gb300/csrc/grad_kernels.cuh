@@ -135,26 +135,36 @@ __device__ __forceinline__ double gamma_bound(const Reps& R, const double* Dsh, 
 // Straight-line gradient kernel (generated VRR/HRR) in precision R for the
 // quartets whose bound Q_ab Q_cd |Gamma| lies in [tau_lo, tau_hi).
 // blockDim.x >= the tile's ket width.
+// Primitive screening: primitive quartet (i|j) is skipped when
+// (qg_i qp_j + qp_i qg_j) |Gamma| < tau_prim (qg: the derivative scale of a
+// primitive pair); tau_prim = 0 keeps every primitive quartet.
 template <class G, typename R>
 __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp, const Tile* __restrict__ tiles,
                                                      const double* __restrict__ Dall, double* __restrict__ grad,
                                                      const R* __restrict__ boys, double tau_lo, double tau_hi,
-                                                     const double* __restrict__ Dsh)
+                                                     const double* __restrict__ Dsh, double tau_prim)
 {
     constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
     __shared__ R sbra[PP_NF][PIMD_MAXPP];
+    __shared__ float sqp[PIMD_MAXPP], sqg[PIMD_MAXPP];
     const Tile t = tiles[blockIdx.x];
     const int ab = t.ab;
     for (int e = threadIdx.x; e < PP_NF * PIMD_MAXPP; e += blockDim.x) {
         const int f = e / PIMD_MAXPP, k = e % PIMD_MAXPP;
         sbra[f][k] = pp_base(P, R(0))[((size_t)f * PIMD_MAXPP + k) * P.n + ab];
     }
+    if (threadIdx.x < PIMD_MAXPP) {
+        sqp[threadIdx.x] = P.qp[(size_t)threadIdx.x * P.n + ab];
+        sqg[threadIdx.x] = P.qg[(size_t)threadIdx.x * P.n + ab];
+    }
     __syncthreads();
     const int cd = t.c0 + threadIdx.x;
     if (cd >= t.c1) return;
     const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
-    const double bound = P.Q[ab] * P.Q[cd] * gamma_bound(Rp, Dsh, t.rep, sa, sb, sc, sd);
+    const double gam = gamma_bound(Rp, Dsh, t.rep, sa, sb, sc, sd);
+    const double bound = P.Q[ab] * P.Q[cd] * gam;
     if (bound < tau_lo || bound >= tau_hi) return;
+    const float gthr = (float)(tau_prim / gam);
     double A[3], B[3], Cc[3], Dd[3];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
@@ -170,9 +180,11 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
     for (int i = 0; i < G::N_accC; i++) accC[i] = R(0);
     const int nbra = P.npp[ab], nket = P.npp[cd];
     for (int j = 0; j < nket; j++) {
+        const float qpj = __ldg(P.qp + (size_t)j * P.n + cd), qgj = __ldg(P.qg + (size_t)j * P.n + cd);
         R ket[PP_NF];
         load_ppn(P, cd, j, ket, PP_NF);
         for (int i = 0; i < nbra; i++) {
+            if (sqg[i] * qpj + sqp[i] * qgj < gthr) continue;
             R bra[PP_NERI];
 #pragma unroll
             for (int f = 0; f < PP_NERI; f++) bra[f] = sbra[f][i];

@@ -72,14 +72,15 @@ void launch_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* 
 // primitive-pair Schwarz factors qp of the listed pairs of one class; reorders
 // each pair's primitive data in pp by descending qp
 void launch_prim_schwarz(int pair_class, const Pairs& P, const Shells& S, const int* list, int n,
-                         const double* boys, double* pp, float* qp, cudaStream_t st);
+                         const double* boys, double* pp, float* qp, float* qg, cudaStream_t st);
 // two-electron gradient of class pair cp: quartets with bound Q_ab Q_cd |Gamma|
 // >= max(tau, fp32_tau) in FP64, those in [tau, fp32_tau) in FP32; variant 0
 // the warp-cooperative kernel, 1 the straight-line kernel with bs threads per
 // block (a class with one variant ignores the choice)
+// (tau_prim: primitive quartets with (qg_i qp_j + qp_i qg_j) |Gamma| below it are skipped; 0 none)
 void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                    const double* D, double* grad, const double* boys, const float* boysf, double tau,
-                   double fp32_tau, const double* Dsh, int variant, int bs, cudaStream_t st);
+                   double fp32_tau, const double* Dsh, int variant, int bs, double tau_prim, cudaStream_t st);
 void grad2e_tapes_upload();   // once per device
 void boys_table_upload(double** dev_tab, float** dev_tabf);
 // FP32 copies for the mixed-precision quartets

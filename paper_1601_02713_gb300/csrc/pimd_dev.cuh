@@ -56,6 +56,8 @@ struct Pairs {
     const float* qp;      // qp[k * n + g]: Schwarz factor sqrt(max |(ij|ij)|) of primitive pair k alone
                           // (contraction coefficients included); the primitive pairs of every shell
                           // pair are stored in descending order of it
+    const float* qg;      // qg[k * n + g] = qp_k 2 sqrt(2 max(a_k, b_k)): the scale of the derivative
+                          // integrals of primitive pair k (d/dA of a Gaussian of exponent a ~ sqrt(2a))
 };
 
 struct Reps {

@@ -576,7 +576,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     ENSURE("npp", npair, d_npp);
     ENSURE("pp", (size_t)PP_NF * PIMD_MAXPP * npair, d_pp);
     ENSURE("Q", npair, d_Q);
-    bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, nullptr, nullptr};
+    bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, nullptr, nullptr, nullptr};
     launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
     ctx->stats.kernel_launches += 2;
     for (int X = 0; X < 6; X++) {
@@ -627,9 +627,10 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
         UPLOAD("Q", Q, d_Q);
         float* d_ppf;
         ENSURE("ppf", (size_t)PP_NF * PIMD_MAXPP * npair, d_ppf);
-        float* d_qp;
+        float *d_qp, *d_qg;
         ENSURE("qp", (size_t)PIMD_MAXPP * npair, d_qp);
-        bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, d_ppf, d_qp};
+        ENSURE("qg", (size_t)PIMD_MAXPP * npair, d_qg);
+        bt.P = Pairs{npair, d_pa, d_pb, d_npp, d_pp, d_Q, d_ppf, d_qp, d_qg};
         launch_pair_data(bt.P, d_npp, d_pp, bt.S, bt.B, ctx->stream);
         // primitive-pair bounds, and each pair's primitives in descending order of them
         for (int X = 0; X < 6; X++) {
@@ -640,7 +641,7 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
             int* d_list;
             std::string nm = "psw_list" + std::to_string(X);
             UPLOAD(nm.c_str(), list, d_list);
-            launch_prim_schwarz(X, bt.P, bt.S, d_list, (int)list.size(), ctx->boys, d_pp, d_qp, ctx->stream);
+            launch_prim_schwarz(X, bt.P, bt.S, d_list, (int)list.size(), ctx->boys, d_pp, d_qp, d_qg, ctx->stream);
             ctx->stats.kernel_launches++;
         }
         launch_to_float(d_pp, d_ppf, (long long)PP_NF * PIMD_MAXPP * npair, ctx->stream);
@@ -1353,7 +1354,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             if (bt.tiles[cp].empty()) continue;
             launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_grad, ctx->boys,
                           ctx->boysf, o->schwarz_tau * 1e-2, o->fp32_tau, bt.Dsh, ctx->grad_var[cp],
-                          ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, ctx->stream);
+                          ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, o->schwarz_tau * 1e-2 * o->prim_screen,
+                          ctx->stream);
             ctx->stats.kernel_launches += o->fp32_tau > 0 ? 2 : 1;
         }
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
@@ -1704,7 +1706,8 @@ extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
                 rc2 = timed(gms, 2, v, use, [&](int cp) {
                     launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_g,
                                   ctx->boys, ctx->boysf, o.schwarz_tau * 1e-2, o.fp32_tau, bt.Dsh, v,
-                                  ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, ctx->stream);
+                                  ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128,
+                                  o.schwarz_tau * 1e-2 * o.prim_screen, ctx->stream);
                 });
             }
         }
