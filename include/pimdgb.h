@@ -68,7 +68,11 @@ typedef struct {
                                fractional-occupation SCF of each isolated neutral atom, 1s 2s 2p
                                configurations, Z <= 10, computed once per basis and element);
                              5 previous MOs where cached, else SAD */
-    int deterministic;    /* reserved, 0 */
+    int deterministic;    /* 0; 1: bitwise-identical results from run to run: the Fock increments,
+                             the nuclear repulsion and the gradient accumulate as 64-bit fixed-point
+                             integers (resolution 2^-48 for the Fock matrix, 2^-40 hartree(/bohr)
+                             for the rest) with integer atomics, whose sum does not depend on the
+                             order of the additions; 0 accumulates with FP64 atomics (last bits vary) */
     int want_gradient;    /* 1 */
     int use_graphs;       /* 1: from the second SCF iteration on, each iteration's kernel sequence
                              (density increment + Fock build; Fock assembly, energy and DIIS error;
@@ -349,6 +353,10 @@ int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, const double
 int pimd_peak_bench(int device, double* fp64_tflops, double* fp32_tflops, double* dmma_tflops);
 
 const char* pimd_strerror(int code);
+/* Detail of the last error a call on ctx returned (which CUDA call failed and
+ * its message, or which argument was rejected); "" if none. The string belongs
+ * to the context and stays valid until its next call. */
+const char* pimd_last_error(const pimd_ctx* ctx);
 
 #ifdef __cplusplus
 }

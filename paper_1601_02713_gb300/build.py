@@ -137,7 +137,7 @@ def generate_sources():
         e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
               "                     const double* D, const float* Df, double* G, const double* boys,",
               "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
-              "                     unsigned long long* cnt, int bs, double tp, cudaStream_t st)",
+              "                     unsigned long long* cnt, int bs, double tp, double fxs, cudaStream_t st)",
               "{",
               "    if (ntiles <= 0) return;",
               "    const double split = fp32_tau > tau ? fp32_tau : tau;"]
@@ -146,19 +146,19 @@ def generate_sources():
                   "        CoopTape t; int W, Wf; size_t bytes, bytesf;",
                   f"        coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
                   f"        jk_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R, tiles,",
-                  "            D, G, boys, split, 1e300, Dsh, cnt, t, tp);",
+                  "            D, G, boys, split, 1e300, Dsh, cnt, t, tp, fxs);",
                   "        if (fp32_tau > tau)",
                   f"            jk_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S, R,",
-                  "                tiles, Df, G, boysf, tau, fp32_tau, Dsh, cnt + 2, t, tp);",
+                  "                tiles, Df, G, boysf, tau, fp32_tau, Dsh, cnt + 2, t, tp, fxs);",
                   "        return;",
                   "    }"]
         if straight_e[nm]:
             e += ["    const int b = bs > 0 ? bs : 128;",
                   f"    jk_kernel<Cls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, G, boys, split, 1e300, Dsh, cnt,",
-                  "                                                      tp);",
+                  "                                                      tp, fxs);",
                   "    if (fp32_tau > tau)",
                   f"        jk_kernel<Cls_{nm}, float><<<ntiles, b, 0, st>>>(P, S, R, tiles, Df, G, boysf, tau, fp32_tau, Dsh,",
-                  "                                                       cnt + 2, tp);"]
+                  "                                                       cnt + 2, tp, fxs);"]
         e.append("}")
         if same:
             e += [f"void launch_schwarz_{nm}(const Pairs& P, const Shells& S, const int* list, int n,",
@@ -188,7 +188,7 @@ def generate_sources():
         gl += [f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                "                        const double* D, double* grad, const double* boys, const float* boysf,",
                "                        double tau, double fp32_tau, const double* Dsh, int variant, int bs,",
-               "                        double tp, cudaStream_t st)",
+               "                        double tp, double fxs, cudaStream_t st)",
                "{",
                "    if (ntiles <= 0) return;",
                "    const double split = fp32_tau > tau ? fp32_tau : tau;"]
@@ -197,19 +197,19 @@ def generate_sources():
                    "        CoopTape t; int W, Wf; size_t bytes, bytesf;",
                    f"        coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
                    f"        grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R,",
-                   "            tiles, D, grad, boys, split, 1e300, Dsh, t, tp);",
+                   "            tiles, D, grad, boys, split, 1e300, Dsh, t, tp, fxs);",
                    "        if (fp32_tau > tau)",
                    f"            grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S,",
-                   "                R, tiles, D, grad, boysf, tau, fp32_tau, Dsh, t, tp);",
+                   "                R, tiles, D, grad, boysf, tau, fp32_tau, Dsh, t, tp, fxs);",
                    "        return;",
                    "    }"]
         if not heavy[nm]:
             gl += ["    const int b = bs > 0 ? bs : 128;",
                    f"    grad2e_kernel<GCls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boys, split, 1e300, Dsh,",
-                   "                                                            tp);",
+                   "                                                            tp, fxs);",
                    "    if (fp32_tau > tau)",
                    f"        grad2e_kernel<GCls_{nm}, float><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boysf, tau, fp32_tau,",
-                   "                                                           Dsh, tp);"]
+                   "                                                           Dsh, tp, fxs);"]
         gl.append("}")
         gl.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_grad_{nm}.cu")
@@ -219,11 +219,11 @@ def generate_sources():
     d = ['#include "internal.h"', "namespace pimd {"]
     sig_jk = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, const float*, double*, "
               "const double*, const float*, double, double, const double*, unsigned long long*, int, double, "
-              "cudaStream_t")
+              "double, cudaStream_t")
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
     sig_psw = "const Pairs&, const Shells&, const int*, int, const double*, double*, float*, float*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-             "const float*, double, double, const double*, int, int, double, cudaStream_t")
+             "const float*, double, double, const double*, int, int, double, double, cudaStream_t")
     for c, nm in zip(classes, names):
         d.append(f"void launch_jk_{nm}({sig_jk});")
         if (c[0], c[1]) == (c[2], c[3]):
@@ -252,8 +252,9 @@ def generate_sources():
     d.append("static const JkFn jk_tab[] = {" + ", ".join(f"launch_jk_{nm}" for nm in names) + "};")
     d.append("void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau, "
-             "double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, double tau_prim, cudaStream_t st)")
-    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, bs, tau_prim, st); }")
+             "double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, double tau_prim, double fxs, "
+             "cudaStream_t st)")
+    d.append("{ jk_tab[cp](P, S, R, tiles, ntiles, D, Df, G, boys, boysf, tau, fp32_tau, Dsh, cnt, bs, tau_prim, fxs, st); }")
     for fn, tab in (("class_pair_coop", coop_e), ("class_pair_straight", straight_e), ("grad_pair_coop", coop_g),
                     ("grad_pair_straight", {nm: not heavy[nm] for nm in names})):
         d.append(f"bool {fn}(int cp)")
@@ -277,8 +278,9 @@ def generate_sources():
 
     d.append("void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, double* grad, const double* boys, const float* boysf, double tau, double fp32_tau, "
-             "const double* Dsh, int variant, int bs, double tau_prim, cudaStream_t st)")
-    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, variant, bs, tau_prim, st); }")
+             "const double* Dsh, int variant, int bs, double tau_prim, double fxs, cudaStream_t st)")
+    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, variant, bs, tau_prim, fxs, "
+             "st); }")
     d.append("void grad2e_tapes_upload() {")
     for nm in names:
         d.append(f"    grad2e_upload_{nm}();")

@@ -234,7 +234,7 @@ __device__ __forceinline__ void coop_sph_to_cart_t(R* buf, R* tmp, int lane)
 // contraction in R, the accumulation into G' in FP64
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void coop_scatter_jk(const R* I, double f, int fa, int fb, int fc, int fd, int N,
-                                                const R* __restrict__ D, double* G, int lane)
+                                                const R* __restrict__ D, double* G, int lane, double fxs)
 {
     constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
 #define IDX(a, b, c, d) ((((a) * nb + (b)) * nc + (c)) * nd + (d))
@@ -244,42 +244,42 @@ __device__ __forceinline__ void coop_scatter_jk(const R* I, double f, int fa, in
         R s = R(0);
         for (int c = 0; c < nc; c++)
             for (int d = 0; d < nd; d++) s += DM(fc + c, fd + d) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s);
+        det_add(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s, fxs);
     }
     for (int e = lane; e < nc * nd; e += 32) {
         const int c = e / nd, d = e % nd;
         R s = R(0);
         for (int a = 0; a < na; a++)
             for (int b = 0; b < nb; b++) s += DM(fa + a, fb + b) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * (double)s);
+        det_add(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * (double)s, fxs);
     }
     for (int e = lane; e < na * nc; e += 32) {
         const int a = e / nc, c = e % nc;
         R s = R(0);
         for (int b = 0; b < nb; b++)
             for (int d = 0; d < nd; d++) s += DM(fb + b, fd + d) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * (double)s);
+        det_add(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * (double)s, fxs);
     }
     for (int e = lane; e < nb * nc; e += 32) {
         const int b = e / nc, c = e % nc;
         R s = R(0);
         for (int a = 0; a < na; a++)
             for (int d = 0; d < nd; d++) s += DM(fa + a, fd + d) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * (double)s);
+        det_add(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * (double)s, fxs);
     }
     for (int e = lane; e < na * nd; e += 32) {
         const int a = e / nd, d = e % nd;
         R s = R(0);
         for (int b = 0; b < nb; b++)
             for (int c = 0; c < nc; c++) s += DM(fb + b, fc + c) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * (double)s);
+        det_add(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * (double)s, fxs);
     }
     for (int e = lane; e < nb * nd; e += 32) {
         const int b = e / nd, d = e % nd;
         R s = R(0);
         for (int a = 0; a < na; a++)
             for (int c = 0; c < nc; c++) s += DM(fa + a, fc + c) * I[IDX(a, b, c, d)];
-        atomicAdd(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * (double)s);
+        det_add(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * (double)s, fxs);
     }
 #undef IDX
 #undef DM
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
                                                       const Rt* __restrict__ boys, double tau_lo, double tau_hi,
                                                       const double* __restrict__ Dsh,
                                                       unsigned long long* __restrict__ cnt, CoopTape tp,
-                                                      double tau_prim)
+                                                      double tau_prim, double fxs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Rt* smem = (Rt*)smem_raw;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
         const int N = R.nbf[r];
         const size_t off = R.moff[r];
         coop_scatter_jk<LA, LB, LC, LD, Rt>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
-                                            Gall + off, lane);
+                                            Gall + off, lane, fxs);
         __syncwarp();
     }
 }
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
                                                           const double* __restrict__ Dall, double* __restrict__ grad,
                                                           const Rt* __restrict__ boys, double tau_lo, double tau_hi,
                                                           const double* __restrict__ Dsh, CoopTape tp,
-                                                          double tau_prim)
+                                                          double tau_prim, double fxs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Rt* smem = (Rt*)smem_raw;
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
         double gd[3][3];
         for (int p = 0; p < 3; p++)
             for (int x = 0; x < 3; x++) gd[p][x] = (double)warp_sum_r<Rt>(gX[p][x]);
-        if (lane == 0) scatter_grad<double>(grad, S, sa, sb, sc, sd, gd[0], gd[1], gd[2]);
+        if (lane == 0) scatter_grad<double>(grad, S, sa, sb, sc, sd, gd[0], gd[1], gd[2], fxs);
         __syncwarp();
     }
 }

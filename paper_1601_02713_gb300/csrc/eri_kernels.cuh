@@ -142,7 +142,6 @@ __device__ __forceinline__ void prim_quartet(const R* bra, const R* ket, PrimQ<R
     g.theta = bra[PP_K] * ket[PP_K] * rs;
 }
 
-__device__ __forceinline__ double atomic_add_d(double* a, double v) { return atomicAdd(a, v); }
 
 // J'_ab of a tile: every lane of the warp holds a quartet with the same bra
 // pair (ab), so the bra-side Coulomb block sum_cd 2f D_cd (ab|cd) is summed
@@ -151,7 +150,7 @@ __device__ __forceinline__ double atomic_add_d(double* a, double v) { return ato
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void bra_coulomb_warp(const R* __restrict__ I, double f, bool work, int fa, int fb,
                                                  int fc, int fd, int N, const R* __restrict__ D,
-                                                 double* __restrict__ G)
+                                                 double* __restrict__ G, double fxs)
 {
     constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
     R Dcd[nc * nd];
@@ -172,7 +171,7 @@ __device__ __forceinline__ void bra_coulomb_warp(const R* __restrict__ I, double
             double v = work ? 2.0 * f * (double)s : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && v != 0.0) atomic_add_d(G + (size_t)(fa + a) * N + fb + b, v);
+            if (lane == 0 && v != 0.0) det_add(G + (size_t)(fa + a) * N + fb + b, v, fxs);
         }
     }
 }
@@ -183,7 +182,7 @@ __device__ __forceinline__ void bra_coulomb_warp(const R* __restrict__ I, double
 // it with bra_coulomb_warp).
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, int fa, int fb, int fc, int fd,
-                                           int N, const R* __restrict__ D, double* __restrict__ G,
+                                           int N, const R* __restrict__ D, double* __restrict__ G, double fxs,
                                            bool bra_j = true)
 {
     constexpr int na = nsph(LA), nb = nsph(LB), nc = nsph(LC), nd = nsph(LD);
@@ -224,7 +223,7 @@ __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, in
                 for (int c = 0; c < nc; c++)
 #pragma unroll
                     for (int d = 0; d < nd; d++) s += Dcd[c * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
-                atomic_add_d(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s);
+                det_add(G + (size_t)(fa + a) * N + fb + b, 2.0 * f * (double)s, fxs);
             }
         }
     }
@@ -237,7 +236,7 @@ __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, in
             for (int a = 0; a < na; a++)
 #pragma unroll
                 for (int b = 0; b < nb; b++) s += Dab[a * nb + b] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * (double)s);
+            det_add(G + (size_t)(fc + c) * N + fd + d, 2.0 * f * (double)s, fxs);
         }
 #pragma unroll
     for (int a = 0; a < na; a++)
@@ -248,7 +247,7 @@ __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, in
             for (int b = 0; b < nb; b++)
 #pragma unroll
                 for (int d = 0; d < nd; d++) s += Dbd[b * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * (double)s);
+            det_add(G + (size_t)(fa + a) * N + fc + c, -0.5 * f * (double)s, fxs);
         }
 #pragma unroll
     for (int b = 0; b < nb; b++)
@@ -259,7 +258,7 @@ __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, in
             for (int a = 0; a < na; a++)
 #pragma unroll
                 for (int d = 0; d < nd; d++) s += Dad[a * nd + d] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * (double)s);
+            det_add(G + (size_t)(fb + b) * N + fc + c, -0.5 * f * (double)s, fxs);
         }
 #pragma unroll
     for (int a = 0; a < na; a++)
@@ -270,7 +269,7 @@ __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, in
             for (int b = 0; b < nb; b++)
 #pragma unroll
                 for (int c = 0; c < nc; c++) s += Dbc[b * nc + c] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * (double)s);
+            det_add(G + (size_t)(fa + a) * N + fd + d, -0.5 * f * (double)s, fxs);
         }
 #pragma unroll
     for (int b = 0; b < nb; b++)
@@ -281,7 +280,7 @@ __device__ __forceinline__ void scatter_jk(const R* __restrict__ I, double f, in
             for (int a = 0; a < na; a++)
 #pragma unroll
                 for (int c = 0; c < nc; c++) s += Dac[a * nc + c] * I[((a * nb + b) * nc + c) * nd + d];
-            atomic_add_d(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * (double)s);
+            det_add(G + (size_t)(fb + b) * N + fd + d, -0.5 * f * (double)s, fxs);
         }
 }
 
@@ -347,13 +346,14 @@ __device__ __forceinline__ int quartet_cart(const R (*sbra)[PIMD_MAXPP], const f
 // (32, 64 or 128, chosen per class pair by the autotuner).
 // cnt: executed quartets and primitive quartets.
 // tau_prim: primitive quartets whose bound qp_i qp_j (density bound) is below
-// it are skipped (0 keeps every primitive quartet).
+// it are skipped (0 keeps every primitive quartet). fxs > 0: G' accumulated as
+// fixed-point integers (det_add).
 template <class C, typename R>
 __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, const Tile* __restrict__ tiles,
                                                  const R* __restrict__ Dall, double* __restrict__ Gall,
                                                  const R* __restrict__ boys, double tau_lo, double tau_hi,
                                                  const double* __restrict__ Dsh, unsigned long long* __restrict__ cnt,
-                                                 double tau_prim)
+                                                 double tau_prim, double fxs)
 {
     __shared__ R sbra[PP_NERI][PIMD_MAXPP];
     __shared__ float sqp[PIMD_MAXPP];
@@ -417,10 +417,10 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
     const int N = R_.nbf[r];
     const size_t off = R_.moff[r];
     bra_coulomb_warp<C::LA, C::LB, C::LC, C::LD, R>(cart, f, work, S.bf[P.sa[ab]], S.bf[P.sb[ab]], S.bf[sc],
-                                                     S.bf[sd], N, Dall + off, Gall + off);
+                                                     S.bf[sd], N, Dall + off, Gall + off, fxs);
     if (work)
         scatter_jk<C::LA, C::LB, C::LC, C::LD, R>(cart, f, S.bf[sa], S.bf[sb], S.bf[sc], S.bf[sd], N, Dall + off,
-                                                  Gall + off, false);
+                                                  Gall + off, fxs, false);
 }
 
 // Schwarz factors: Q_ab = sqrt(max over functions of (mn|mn)), one thread per pair

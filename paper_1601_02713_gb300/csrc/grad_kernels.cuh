@@ -110,16 +110,16 @@ struct ArrAcc {
 
 template <typename R>
 __device__ __forceinline__ void scatter_grad(double* grad, const Shells& S, int sa, int sb, int sc, int sd,
-                                             const R gA[3], const R gB[3], const R gC[3])
+                                             const R gA[3], const R gB[3], const R gC[3], double fxs)
 {
     const int aa = S.atom[sa], ab = S.atom[sb], ac = S.atom[sc], ad = S.atom[sd];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
         const double a = gA[x], b = gB[x], c = gC[x];
-        atomicAdd(grad + 3 * aa + x, a);
-        atomicAdd(grad + 3 * ab + x, b);
-        atomicAdd(grad + 3 * ac + x, c);
-        atomicAdd(grad + 3 * ad + x, -(a + b + c));
+        det_add(grad + 3 * aa + x, a, fxs);
+        det_add(grad + 3 * ab + x, b, fxs);
+        det_add(grad + 3 * ac + x, c, fxs);
+        det_add(grad + 3 * ad + x, -(a + b + c), fxs);
     }
 }
 
@@ -142,7 +142,7 @@ template <class G, typename R>
 __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp, const Tile* __restrict__ tiles,
                                                      const double* __restrict__ Dall, double* __restrict__ grad,
                                                      const R* __restrict__ boys, double tau_lo, double tau_hi,
-                                                     const double* __restrict__ Dsh, double tau_prim)
+                                                     const double* __restrict__ Dsh, double tau_prim, double fxs)
 {
     constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
     __shared__ R sbra[PP_NF][PIMD_MAXPP];
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
             contract_deriv<LA, LB, LC, LD, 2>(Gc, ArrAcc<R>{up}, ArrAcc<R>{up}, gC);
         }
     }
-    scatter_grad(grad, S, sa, sb, sc, sd, gA, gB, gC);
+    scatter_grad(grad, S, sa, sb, sc, sd, gA, gB, gC, fxs);
 }
 
 }  // namespace pimd

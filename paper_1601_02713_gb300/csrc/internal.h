@@ -37,11 +37,17 @@ void launch_one_electron(const Pairs& P, const Shells& S, const BasisPrimDev& B,
 // one-electron gradient: 2 sum D dh/dA - 2 sum W dS/dA (bra derivatives over ordered pairs)
 // plus the Hellmann-Feynman term, accumulated into grad[natom_total][3]
 void launch_grad_1e(const Pairs& P, const Shells& S, const BasisPrimDev& B, const AtomsDev& At, const Reps& R,
-                    const double* D, const double* W, double* grad, const double* boys, cudaStream_t st);
+                    const double* D, const double* W, double* grad, const double* boys, double fxs,
+                    cudaStream_t st);
 
 // nuclear repulsion energy per replica (added into enn[rep]) and its gradient
+// (fxs > 0: enn and grad are fixed-point accumulators, see det_add)
 void launch_vnn(const AtomsDev& At, int natom_total, const int* atom_rep, double* enn, double* grad,
-                cudaStream_t st);
+                cudaStream_t st, double fxs = 0.0);
+// in-place conversion of n values between FP64 and the fixed-point integers
+// of det_add (scale fxs)
+void launch_double_to_fixed(double* a, long long n, double fxs, cudaStream_t st);
+void launch_fixed_to_double(double* a, long long n, double fxs, cudaStream_t st);
 
 // ERI kernels, per class pair index (0..20 over (X, Y), X >= Y in the order
 // ss, ps, pp, ds, dp, dd)
@@ -57,9 +63,10 @@ long long class_vrr_flops(int cp);
 // kernel, bs = 0 for the warp-cooperative kernel (a class with one variant
 // ignores the choice)
 // tau_prim: primitive quartets with qp_i qp_j max|D block| below it are skipped (0: none)
+// fxs > 0: G accumulated as fixed-point integers scaled by fxs (deterministic mode, det_add)
 void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau,
-               double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, double tau_prim,
+               double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, double tau_prim, double fxs,
                cudaStream_t st);
 // kernel variants generated for a class pair: the warp-cooperative tape
 // kernel and the straight-line kernel, for the Fock build and the gradient
@@ -80,7 +87,8 @@ void launch_prim_schwarz(int pair_class, const Pairs& P, const Shells& S, const 
 // (tau_prim: primitive quartets with (qg_i qp_j + qp_i qg_j) |Gamma| below it are skipped; 0 none)
 void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                    const double* D, double* grad, const double* boys, const float* boysf, double tau,
-                   double fp32_tau, const double* Dsh, int variant, int bs, double tau_prim, cudaStream_t st);
+                   double fp32_tau, const double* Dsh, int variant, int bs, double tau_prim, double fxs,
+                   cudaStream_t st);
 void grad2e_tapes_upload();   // once per device
 void boys_table_upload(double** dev_tab, float** dev_tabf);
 // FP32 copies for the mixed-precision quartets

@@ -5,6 +5,8 @@
 // SCF has finished are skipped through the active mask.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "pimdgb.h"
 
@@ -549,6 +551,28 @@ void launch_delta_density(const RepMat* rm, int nrep, const double* D, double* D
                           const int* mode, cudaStream_t st)
 {
     delta_density_kernel<<<dim3(64, nrep), 256, 0, st>>>(rm, D, Dprev, dD, G, mode);
+}
+
+__global__ void to_fixed_kernel(double* a, long long n, double fxs)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        ((long long*)a)[i] = __double2ll_rn(a[i] * fxs);
+}
+
+__global__ void from_fixed_kernel(double* a, long long n, double fxs)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = (double)((const long long*)a)[i] / fxs;
+}
+
+void launch_double_to_fixed(double* a, long long n, double fxs, cudaStream_t st)
+{
+    if (n > 0) to_fixed_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(a, n, fxs);
+}
+
+void launch_fixed_to_double(double* a, long long n, double fxs, cudaStream_t st)
+{
+    if (n > 0) from_fixed_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(a, n, fxs);
 }
 
 void gather_xyz(const double* atom_xyz, const int* shell_atom, int nshell, double* shell_xyz, cudaStream_t st)

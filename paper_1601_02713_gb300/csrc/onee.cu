@@ -376,7 +376,7 @@ __global__ void one_e_kernel(Pairs P, Shells S, BasisPrimDev B, AtomsDev At, Rep
 // derivative of the bra Gaussian: d/dA_x g_a = 2 alpha g_{a+1_x} - a_x g_{a-1_x}
 // One thread per (pair, orientation).
 __global__ void grad_1e_kernel(Pairs P, Shells S, BasisPrimDev B, AtomsDev At, Reps R, const double* D,
-                               const double* W, double* grad, const double* boys)
+                               const double* W, double* grad, const double* boys, double fxs)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * P.n) return;
@@ -576,13 +576,13 @@ __global__ void grad_1e_kernel(Pairs P, Shells S, BasisPrimDev B, AtomsDev At, R
             double s = 0.0;
             for (int k = 0; k < nac * nbc; k++) s += 2.0 * Dc[k] * dV[x][k];
             ga[x] += s;
-            atomicAdd(grad + 3 * c + x, -s);
+            det_add(grad + 3 * c + x, -s, fxs);
         }
     }
-    for (int x = 0; x < 3; x++) atomicAdd(grad + 3 * atom_a + x, ga[x]);
+    for (int x = 0; x < 3; x++) det_add(grad + 3 * atom_a + x, ga[x], fxs);
 }
 
-__global__ void vnn_kernel(AtomsDev At, int natom, const int* atom_rep, double* enn, double* grad)
+__global__ void vnn_kernel(AtomsDev At, int natom, const int* atom_rep, double* enn, double* grad, double fxs)
 {
     const int A = blockIdx.x * blockDim.x + threadIdx.x;
     if (A >= natom) return;
@@ -601,9 +601,9 @@ __global__ void vnn_kernel(AtomsDev At, int natom, const int* atom_rep, double* 
         e += 0.5 * zz / rr;
         for (int x = 0; x < 3; x++) g[x] -= zz * d[x] / (rr * r2);
     }
-    atomicAdd(enn + r, e);
+    det_add(enn + r, e, fxs);
     if (grad)
-        for (int x = 0; x < 3; x++) atomicAdd(grad + 3 * A + x, g[x]);
+        for (int x = 0; x < 3; x++) det_add(grad + 3 * A + x, g[x], fxs);
 }
 
 __global__ void boys_eval_kernel(int n, int m, const double* T, double* F, const double* boys)
@@ -689,17 +689,18 @@ void launch_one_electron(const Pairs& P, const Shells& S, const BasisPrimDev& B,
 }
 
 void launch_grad_1e(const Pairs& P, const Shells& S, const BasisPrimDev& B, const AtomsDev& At, const Reps& R,
-                    const double* D, const double* W, double* grad, const double* boys, cudaStream_t st)
+                    const double* D, const double* W, double* grad, const double* boys, double fxs,
+                    cudaStream_t st)
 {
     if (P.n == 0) return;
-    grad_1e_kernel<<<(2 * P.n + 63) / 64, 64, 0, st>>>(P, S, B, At, R, D, W, grad, boys);
+    grad_1e_kernel<<<(2 * P.n + 63) / 64, 64, 0, st>>>(P, S, B, At, R, D, W, grad, boys, fxs);
 }
 
 void launch_vnn(const AtomsDev& At, int natom_total, const int* atom_rep, double* enn, double* grad,
-                cudaStream_t st)
+                cudaStream_t st, double fxs)
 {
     if (natom_total == 0) return;
-    vnn_kernel<<<(natom_total + 127) / 128, 128, 0, st>>>(At, natom_total, atom_rep, enn, grad);
+    vnn_kernel<<<(natom_total + 127) / 128, 128, 0, st>>>(At, natom_total, atom_rep, enn, grad, fxs);
 }
 
 void launch_boys_eval(int n, int m, const double* T, double* F, const double* boys, cudaStream_t st)

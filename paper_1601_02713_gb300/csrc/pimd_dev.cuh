@@ -76,6 +76,23 @@ __device__ __forceinline__ double shell_bound(const Reps& R, const double* __res
     return __ldg(Dsh + R.dsoff[r] + (size_t)(a - a0) * n + (b - a0));
 }
 
+// Accumulation into a shared FP64 result: *p += v with an FP64 atomic, or,
+// for bitwise-reproducible runs (fxs > 0), as a 64-bit fixed-point integer
+// (v scaled by fxs and rounded) with an integer atomic, which is associative,
+// so the sum does not depend on the order of the additions. The buffer then
+// holds integers until it is converted back (fixed_to_double).
+__device__ __forceinline__ void det_add(double* p, double v, double fxs)
+{
+    if (fxs > 0.0)
+        atomicAdd((unsigned long long*)p, (unsigned long long)__double2ll_rn(v * fxs));
+    else
+        atomicAdd(p, v);
+}
+// fixed-point scales of the deterministic mode: Fock increments (|G'| < 2^15),
+// gradients and nuclear-repulsion energies (|.| < 2^23)
+constexpr double kFixG = 281474976710656.0;     // 2^48
+constexpr double kFixGrad = 1099511627776.0;    // 2^40
+
 // one block of quartets: bra pair ab with ket pairs [c0, c1)
 struct Tile {
     int ab, c0, c1, rep;

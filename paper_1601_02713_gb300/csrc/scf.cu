@@ -354,6 +354,12 @@ extern "C" const char* pimd_strerror(int code)
     }
 }
 
+extern "C" const char* pimd_last_error(const pimd_ctx* ctx)
+{
+    if (!ctx) return "";
+    return ctx->last_error.c_str();
+}
+
 extern "C" int pimd_last_trace(const pimd_ctx* ctx, int rep, int maxit, double* energy, double* error,
                                int* full_build)
 {
@@ -843,8 +849,10 @@ static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, co
 // the quartets screened by Q_ab Q_cd max|M block| >= tau; those below fp32_tau
 // (if > 0) are evaluated in FP32 from Mf, an FP32 copy of M made here
 static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32_tau, const double* M,
-                      double tau_prim)
+                      double tau_prim, double fxs)
 {
+    // deterministic mode: the build accumulates into G' as fixed-point integers
+    if (fxs > 0) launch_double_to_fixed(m.G, bt.mtot, fxs, ctx->stream);
     launch_shell_bounds(bt.S, bt.R, bt.nrep, bt.maxsh, M, bt.Dsh, bt.R.active, ctx->stream);
     ctx->stats.kernel_launches++;
     float* Mf = nullptr;
@@ -856,8 +864,12 @@ static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32
     for (int cp = 0; cp < n_class_pairs(); cp++) {
         if (bt.tiles[cp].empty()) continue;
         launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), M, Mf, m.G, ctx->boys, ctx->boysf,
-                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->tile_w[cp], tau_prim, ctx->stream);
+                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->tile_w[cp], tau_prim, fxs, ctx->stream);
         ctx->stats.kernel_launches += fp32_tau > tau ? 2 : 1;
+    }
+    if (fxs > 0) {
+        launch_fixed_to_double(m.G, bt.mtot, fxs, ctx->stream);
+        ctx->stats.kernel_launches += 2;
     }
     return PIMD_OK;
 }
@@ -963,7 +975,9 @@ static int sad_atomic(pimd_ctx* ctx, const pimd_basis* basis, const std::vector<
     bool conv = false;
     for (int it = 1; it <= 200 && !conv; it++) {
         launch_delta_density(m.rm, n, m.D, m.Dp, m.dD, m.G, d_mode, st);
-        if ((rc = fock_build(ctx, bt, m, 1e-12, 0.0, m.dD, 0.0))) return rc;
+        // fixed-point accumulation: the cached atomic densities do not depend on
+        // the order of the additions
+        if ((rc = fock_build(ctx, bt, m, 1e-12, 0.0, m.dD, 0.0, kFixG))) return rc;
         launch_fock_assemble(m.rm, n, m.H, m.G, m.F, m.active, st);
         launch_copy_mats(m.rm, n, m.F, m.Fb, nullptr, st);
         if ((rc = density())) return set_err(ctx, rc, "SAD: atom without a 2p shell in the basis");
@@ -1126,13 +1140,16 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         add_mats(m.rm, nrep, m.T, m.V, m.H, ctx->stream);
     }
     CK(cudaMemsetAsync(m.enn, 0, sizeof(double) * nrep, ctx->stream));
+    // deterministic mode: fixed-point accumulation of G', V_nn and the gradient
+    const double fx_g = o->deterministic ? kFixG : 0.0, fx_grad = o->deterministic ? kFixGrad : 0.0;
     {
         std::vector<int> atom_rep;
         for (int r = 0; r < nrep; r++)
             for (int i = 0; i < bt.natom[r]; i++) atom_rep.push_back(r);
         int* d_ar;
         UPLOAD("atom_rep2", atom_rep, d_ar);
-        launch_vnn(bt.At, bt.atom0[nrep], d_ar, m.enn, nullptr, ctx->stream);
+        launch_vnn(bt.At, bt.atom0[nrep], d_ar, m.enn, nullptr, ctx->stream, fx_grad);
+        if (fx_grad > 0) launch_fixed_to_double(m.enn, nrep, fx_grad, ctx->stream);
     }
     // X = S^{-1/2}
     launch_jacobi(m.rm, nrep, m.S, m.Cp, m.Ev, m.ldE, m.work, nullptr, 0, ctx->stream, m.jnc);
@@ -1247,7 +1264,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         rc = run_seg(ctx, seg_fock, graphs, [&]() -> int {
             launch_delta_density(m.rm, nrep, m.D, m.Dp, m.dD, m.G, d_mode, ctx->stream);
             ctx->stats.kernel_launches++;
-            return fock_build(ctx, bt, m, o->schwarz_tau, o->fp32_tau, m.dD, o->schwarz_tau * o->prim_screen);
+            return fock_build(ctx, bt, m, o->schwarz_tau, o->fp32_tau, m.dD, o->schwarz_tau * o->prim_screen,
+                              fx_g);
         });
         if (rc) return rc;
         CK(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -1341,12 +1359,12 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     if (o->want_gradient && d_grad) {
         const int natot = bt.atom0[nrep];
         CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * natot * 3, ctx->stream));
-        launch_grad_1e(bt.P, bt.S, bt.B, bt.At, bt.R, m.D, m.W, d_grad, ctx->boys, ctx->stream);
+        launch_grad_1e(bt.P, bt.S, bt.B, bt.At, bt.R, m.D, m.W, d_grad, ctx->boys, fx_grad, ctx->stream);
         {
             int* d_ar = (int*)ctx->bufs["atom_rep2"].p;
             double* d_dummy;
             ENSURE("enn_dummy", nrep, d_dummy);
-            launch_vnn(bt.At, natot, d_ar, d_dummy, d_grad, ctx->stream);
+            launch_vnn(bt.At, natot, d_ar, d_dummy, d_grad, ctx->stream, fx_grad);
         }
         CK(cudaEventRecord(ctx->ev[4], ctx->stream));
         launch_shell_bounds(bt.S, bt.R, nrep, bt.maxsh, m.D, bt.Dsh, nullptr, ctx->stream);
@@ -1355,11 +1373,12 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_grad, ctx->boys,
                           ctx->boysf, o->schwarz_tau * 1e-2, o->fp32_tau, bt.Dsh, ctx->grad_var[cp],
                           ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, o->schwarz_tau * 1e-2 * o->prim_screen,
-                          ctx->stream);
+                          fx_grad, ctx->stream);
             ctx->stats.kernel_launches += o->fp32_tau > 0 ? 2 : 1;
         }
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
-        ctx->stats.kernel_launches += 3;
+        if (fx_grad > 0) launch_fixed_to_double(d_grad, natot * 3, fx_grad, ctx->stream);
+        ctx->stats.kernel_launches += fx_grad > 0 ? 4 : 3;
     }
     // MO cache (and the final Fock matrix)
     for (int r = 0; r < nrep; r++) {
@@ -1676,7 +1695,7 @@ extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
             if (!bt.tiles[cp].empty())
                 launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, Mf, m.G, ctx->boys,
                           ctx->boysf, o.schwarz_tau, o.fp32_tau, bt.Dsh, bt.cnt + 4 * cp, cand[ci],
-                          o.schwarz_tau * o.prim_screen, ctx->stream);
+                          o.schwarz_tau * o.prim_screen, 0.0, ctx->stream);
         });
     }
     double best = 0.0;
@@ -1707,7 +1726,7 @@ extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
                     launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_g,
                                   ctx->boys, ctx->boysf, o.schwarz_tau * 1e-2, o.fp32_tau, bt.Dsh, v,
                                   ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128,
-                                  o.schwarz_tau * 1e-2 * o.prim_screen, ctx->stream);
+                                  o.schwarz_tau * 1e-2 * o.prim_screen, 0.0, ctx->stream);
                 });
             }
         }
@@ -1747,7 +1766,7 @@ extern "C" int pimd_fock_dev(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
     {
         pimd_scf_opts d;
         pimd_scf_opts_default(&d);
-        if ((rc = fock_build(ctx, bt, m, schwarz_tau, fp32_tau, m.D, schwarz_tau * d.prim_screen))) return rc;
+        if ((rc = fock_build(ctx, bt, m, schwarz_tau, fp32_tau, m.D, schwarz_tau * d.prim_screen, 0.0))) return rc;
     }
     // G_out = G' + G'^T
     CK(cudaMemsetAsync(m.H, 0, sizeof(double) * bt.mtot, ctx->stream));

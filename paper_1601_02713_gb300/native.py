@@ -40,9 +40,9 @@ class PimdStats(ctypes.Structure):
 
 
 class PimdError(RuntimeError):
-    def __init__(self, code, what=""):
+    def __init__(self, code, what="", detail=""):
         self.code = code
-        super().__init__(f"{what}: {strerror(code)} ({code})")
+        super().__init__(f"{what}: {strerror(code)} ({code})" + (f" [{detail}]" if detail else ""))
 
 
 _lib = None
@@ -117,6 +117,8 @@ def load(path: str | None = None):
                                        ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P]
     lib.pimd_strerror.argtypes = [ctypes.c_int]
     lib.pimd_strerror.restype = ctypes.c_char_p
+    lib.pimd_last_error.argtypes = [_P]
+    lib.pimd_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -133,10 +135,13 @@ def _ip(a):
     return a.ctypes.data_as(_I)
 
 
-def _check(rc, what, allow_notconv=False):
+def _check(rc, what, allow_notconv=False, ctx=None):
     if rc == PIMD_OK or (allow_notconv and rc == PIMD_ENOTCONV):
         return rc
-    raise PimdError(rc, what)
+    detail = ""
+    if ctx is not None and getattr(ctx, "handle", None):
+        detail = load().pimd_last_error(ctx.handle).decode()
+    raise PimdError(rc, what, detail)
 
 
 def scf_opts(**kw) -> PimdScfOpts:
@@ -213,7 +218,7 @@ def pimd_bo_forces(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | No
     rc = load().pimd_bo_forces(ctx.handle, nrep, natom, _ip(Z), _dp(X), basis.handle, ctypes.byref(opts), _dp(E),
                                _dp(G), info)
     if check:
-        _check(rc, "pimd_bo_forces", allow_notconv=True)
+        _check(rc, "pimd_bo_forces", allow_notconv=True, ctx=ctx)
     return E, G, _infos(info), rc
 
 
@@ -230,7 +235,7 @@ def string_images_forces(ctx: Context, basis: Basis, natom_of_img, Z_concat, coo
     rc = load().string_images_forces(ctx.handle, nimg, _ip(nat), _ip(Z), _dp(X), basis.handle, ctypes.byref(opts),
                                      _dp(E), _dp(G), info)
     if check:
-        _check(rc, "string_images_forces", allow_notconv=True)
+        _check(rc, "string_images_forces", allow_notconv=True, ctx=ctx)
     return E, G, _infos(info), rc
 
 
@@ -247,7 +252,7 @@ def pimd_bo_forces_dev(ctx: Context, basis: Basis, Z, coords_dev, energies_dev, 
                                    _P(gradients_dev.data_ptr() if gradients_dev is not None else 0), info,
                                    _P(stream))
     if check:
-        _check(rc, "pimd_bo_forces_dev", allow_notconv=True)
+        _check(rc, "pimd_bo_forces_dev", allow_notconv=True, ctx=ctx)
     return _infos(info), rc
 
 
@@ -262,7 +267,7 @@ def string_images_forces_dev(ctx: Context, basis: Basis, natom_of_img, Z_concat,
                                          _P(gradients_dev.data_ptr() if gradients_dev is not None else 0), info,
                                          _P(stream))
     if check:
-        _check(rc, "string_images_forces_dev", allow_notconv=True)
+        _check(rc, "string_images_forces_dev", allow_notconv=True, ctx=ctx)
     return _infos(info), rc
 
 
@@ -452,7 +457,7 @@ class GuessModel:
         info = (PimdInfo * X.shape[0])()
         _check(load().pimd_guess_add_data(self.handle, ctx.handle, X.shape[0], X.shape[1], _ip(Z), _dp(X),
                                           basis.handle, ctypes.byref(opts), ctypes.cast(info, _P)),
-               "pimd_guess_add_data")
+               "pimd_guess_add_data", ctx=ctx)
         return _infos(info)
 
     def clear_data(self):
