@@ -43,16 +43,19 @@ constexpr int COOP_NG0 = 20;
 constexpr int COOP_CT = 37;
 constexpr int COOP_KMAX = 5;
 
-// coefficient table ct of one primitive from its geometry g (lane-parallel)
+// coefficient table ct of one primitive from its geometry g (lane-parallel;
+// the table has more entries than a warp has lanes)
 template <typename R>
 __device__ __forceinline__ void coop_fill_ct(const R* g, R* ct, int lane)
 {
-    if (lane < 12) {
-        ct[lane] = g[lane];
-    } else if (lane < COOP_CT) {
-        const int t = (lane - 12) / COOP_KMAX, k = (lane - 12) % COOP_KMAX + 1;
-        const R v = R(k) * g[12 + t];
-        ct[lane] = (t == 1 || t == 3) ? -v : v;
+    for (int e = lane; e < COOP_CT; e += 32) {
+        if (e < 12) {
+            ct[e] = g[e];
+        } else {
+            const int t = (e - 12) / COOP_KMAX, k = (e - 12) % COOP_KMAX + 1;
+            const R v = R(k) * g[12 + t];
+            ct[e] = (t == 1 || t == 3) ? -v : v;
+        }
     }
 }
 

@@ -348,3 +348,27 @@ def test_diels_alder_images_against_stored_oracle(ctx, spd, fp32_tau):
         assert np.abs(Xc[off[k]:off[k + 1]] - np.array(g["coords_bohr"])).max() < 1e-12
         assert abs(E[k] - g["energy"]) < etol, (g["replica"], E[k] - g["energy"])
         assert np.abs(G[off[k]:off[k + 1]] - np.array(g["gradient"])).max() < gtol
+
+
+def test_deterministic_mode_is_bitwise_reproducible(spd):
+    """deterministic = 1: the Fock increments, V_nn and the gradient are summed
+    as fixed-point integers, so repeated calls (fresh contexts, the same
+    inputs) give bitwise-identical energies and gradients, within round-off
+    of the FP64-atomic default."""
+    bas, B = spd
+    reps, _ = inputs.workload("water8_spd_32beads", nrep=3)
+    Z, X = reps.stacked()
+    out = []
+    for _ in range(2):
+        c = native.Context(0)
+        E, G, info, rc = native.pimd_bo_forces(c, B, Z, X, native.scf_opts(deterministic=1))
+        assert rc == 0 and all(i["converged"] for i in info)
+        out.append((E, G))
+        c.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    c = native.Context(0)
+    E0, G0, _, rc = native.pimd_bo_forces(c, B, Z, X)
+    c.close()
+    assert rc == 0
+    np.testing.assert_allclose(out[0][0], E0, atol=1e-9, rtol=0)
+    np.testing.assert_allclose(out[0][1], G0, atol=1e-8, rtol=0)
