@@ -73,14 +73,36 @@ __device__ __forceinline__ double boys_exp_tail(double T, const double* __restri
     return theta * __ldg(tab + BOYS_EXP_OFF + k) * e;
 }
 
+// Nearest grid index k = round(T * BOYS_GRID) and the offset x = T_k - T,
+// for 0 <= T < 2^31 / BOYS_GRID: adding 1.5 * 2^52 to T * BOYS_GRID rounds it
+// to an integer (the spacing of doubles there is 1), which then sits in the
+// low word; three FP64 operations, no conversion instructions.
+__device__ __forceinline__ int boys_grid_point(double T, double& x)
+{
+    constexpr double kRound = 6755399441055744.0;   // 1.5 * 2^52
+    const double s = fma(T, (double)BOYS_GRID, kRound);
+    const double kd = s - kRound;
+    x = fma(kd, 1.0 / BOYS_GRID, -T);
+    return __double2loint(s);
+}
+
+// T < BOYS_TMAX for T >= 0, decided on the high word (integer compare): the
+// high words of non-negative doubles are ordered like the values, and 40.0
+// has an all-zero low word
+__device__ __forceinline__ bool boys_in_table(double T)
+{
+    static_assert(BOYS_TMAX == 40.0, "high word of BOYS_TMAX");
+    return __double2hiint(T) < 0x40440000;
+}
+
 // F[m] = theta F_m(T), m = 0..L (L a compile-time order)
 template <int L>
 __device__ __forceinline__ void boys_eval(double T, const double* __restrict__ tab, double theta, double* F)
 {
     constexpr double kHalfSqrtPi = 0.88622692545275801365;   // sqrt(pi) / 2
-    if (T < BOYS_TMAX) {
-        const int k = __double2int_rn(T * BOYS_GRID);
-        const double x = k * (1.0 / BOYS_GRID) - T;
+    if (boys_in_table(T)) {
+        double x;
+        const int k = boys_grid_point(T, x);
         const double* t = tab + ((size_t)k * BOYS_MT + L) * BOYS_NTAYLOR;
         double f = __ldg(t + BOYS_NTAYLOR - 1);
 #pragma unroll
@@ -171,9 +193,9 @@ __device__ __forceinline__ void boys_eval_n(int L, float T, const float* __restr
 __device__ __forceinline__ void boys_eval_n(int L, double T, const double* __restrict__ tab, double theta, double* F)
 {
     constexpr double kHalfSqrtPi = 0.88622692545275801365;   // sqrt(pi) / 2
-    if (T < BOYS_TMAX) {
-        const int k = __double2int_rn(T * BOYS_GRID);
-        const double x = k * (1.0 / BOYS_GRID) - T;
+    if (boys_in_table(T)) {
+        double x;
+        const int k = boys_grid_point(T, x);
         const double* t = tab + ((size_t)k * BOYS_MT + L) * BOYS_NTAYLOR;
         double f = __ldg(t + BOYS_NTAYLOR - 1);
 #pragma unroll

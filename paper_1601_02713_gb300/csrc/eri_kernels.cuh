@@ -107,7 +107,24 @@ struct PrimQ {
 };
 typedef PrimQ<double> PrimQuartet;
 
-__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+// 1/sqrt(x) for normal positive x with |log2 x| < 126 (p + q of two Gaussian
+// exponents): a single-precision estimate from the hardware approximation
+// (operand and result moved between the formats with integer operations on
+// the exponent and mantissa fields), then one Newton step for f(y) = y^-2 - x
+// carried to second order: with e = 1 - x y0^2, y = y0 (1 + e/2 + 3e^2/8), so
+// the relative error goes from |e| < 2^-20 to about (5/16) e^3 < 2^-61.
+__device__ __forceinline__ double rsqrt_r(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    // float with the top 23 mantissa bits of x (exponent rebias 1023 -> 127)
+    const float xf = __int_as_float(((hi - (896 << 20)) << 3) | ((unsigned)lo >> 29));
+    const int yb = __float_as_int(rsqrtf(xf));
+    const double y0 = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
+    const double t = x * y0;
+    const double e = fma(-t, y0, 1.0);
+    const double c = fma(0.375, e, 0.5);
+    return fma(y0 * e, c, y0);
+}
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 
 // bra/ket: the first PP_NERI primitive-pair fields (p, P, K, P - A, 1/(2p), 1/(2p^2))

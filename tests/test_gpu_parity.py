@@ -372,3 +372,63 @@ def test_deterministic_mode_is_bitwise_reproducible(spd):
     assert rc == 0
     np.testing.assert_allclose(out[0][0], E0, atol=1e-9, rtol=0)
     np.testing.assert_allclose(out[0][1], G0, atol=1e-8, rtol=0)
+
+
+def _water32(nrep=1):
+    reps, _ = inputs.workload("water32_spd_16beads", nrep=nrep)
+    return reps.stacked()
+
+
+def test_water32_full_fock_build_against_oracle(ctx, spd):
+    """(H2O)32, 768 functions: one whole Fock build of bead 0 for the
+    oracle's core-Hamiltonian density, against the oracle's build stored by
+    tests/golden/make_fock_golden.py (every element through G v for two
+    seeded vectors, the diagonal, two full rows, v^T G v and tr(D G))."""
+    import importlib.util
+    import os
+    g = _golden("water32_spd_16beads_rep0_fock.json")
+    spec = importlib.util.spec_from_file_location(
+        "make_fock_golden", os.path.join(os.path.dirname(__file__), "golden", "make_fock_golden.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    bas, B = spd
+    Z, Xs = _water32()
+    assert np.abs(Xs[0] - np.array(g["coords_bohr"])).max() < 1e-12
+    ob, D = mk.core_density(bas, Z, Xs[0])
+    Dt = torch.tensor(D[None], device="cuda")
+    Gt = torch.zeros_like(Dt)
+    native.pimd_fock_dev(ctx, B, Z, Xs[:1], Dt, Gt, 1e-12, 0.0)
+    G = Gt[0].cpu().numpy()
+    scale = np.abs(np.array(g["diag"])).max()
+    for v, ref in zip(mk.probe_vectors(ob.nbf), g["Gv"]):
+        assert np.abs(G @ v - np.array(ref)).max() < 1e-8 * scale * np.sqrt(ob.nbf)
+    assert np.abs(np.diag(G) - np.array(g["diag"])).max() < 1e-9 * scale
+    for r, row in g["rows"].items():
+        assert np.abs(G[int(r)] - np.array(row)).max() < 1e-9 * scale
+    assert abs(np.sum(D * G) - g["tr_DG"]) < 1e-8 * abs(g["tr_DG"])
+
+
+def test_water32_bead_invariance_and_mixed_precision(ctx, spd):
+    """(H2O)32 on the GPU alone, properties that hold at any size: the FP64
+    energy of a bead is invariant under a rigid rotation of it, and the
+    mixed-precision energy and gradient stay within the mixed tolerances
+    (1e-6 Eh, 1e-5 Eh/bohr) of the FP64 path on the same bead."""
+    bas, B = spd
+    Z, Xs = _water32()
+    X = Xs[:1]
+    E64, G64, i64, rc = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=4))
+    assert rc == 0 and i64[0]["converged"]
+    E32, G32, i32, rc = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=4, fp32_tau=1e-6))
+    assert rc == 0 and i32[0]["converged"]
+    assert abs(E32[0] - E64[0]) < 1e-6
+    assert np.abs(G32 - G64).max() < 1e-5
+    ang = 0.61
+    c, s = np.cos(ang), np.sin(ang)
+    Rm = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]]) @ np.array([[1.0, 0.0, 0.0], [0.0, c, s],
+                                                                          [0.0, -s, c]])
+    Xr = X @ Rm.T + np.array([0.7, -1.1, 0.4])
+    Er, Gr, ir, rc = native.pimd_bo_forces(ctx, B, Z, Xr, native.scf_opts(guess=4))
+    assert rc == 0 and ir[0]["converged"]
+    assert abs(Er[0] - E64[0]) < 1e-8
+    # the gradient rotates with the molecule
+    assert np.abs(Gr[0] - G64[0] @ Rm.T).max() < 1e-6
