@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--train-clusters", type=int, default=8)
     ap.add_argument("--train-beads", type=int, default=16)
     ap.add_argument("--train-epochs", type=int, default=400)
+    ap.add_argument("--eval-water32", type=int, default=0,
+                    help="guess study: also start this many (H2O)32 beads (mixed precision) from SAD and from the "
+                         "learned density")
     return ap.parse_args()
 
 
@@ -284,6 +287,18 @@ def run_guess_study(args):
         run(X0, 4, tau)
         E1, G1, it, v = run(X1, 1, tau)
         rows.append(("batched", prec, "previous-step MOs (next MD step)", it, v, None, None))
+    if args.eval_water32 > 0:
+        reps32, _ = inputs.workload("water32_spd_16beads", nrep=args.eval_water32)
+        Z32, X32 = reps32.stacked()
+        for guess, gname in ((4, "SAD"), (2, "learned")):
+            ctx.clear_guess()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            E, G, info, _ = native.pimd_bo_forces(ctx, basis, Z32, X32, native.scf_opts(guess=guess, fp32_tau=1e-6))
+            dt = time.perf_counter() - t
+            assert all(i["converged"] for i in info)
+            it = float(np.mean([i["iterations"] for i in info]))
+            rows.append(("batched (H2O)32", "mixed", gname, it, len(X32) / dt, None, None))
     out = {"study": "learned SCF guess", "workload": args.workload, "beads": nrep, "basis": kind,
            "training": {"geometries": ntrain, "system": f"(H2O){len(Z) // 3} seeded clusters 500..",
                         "data_s": t_data, "epochs": args.train_epochs, "train_s": t_train,

@@ -26,21 +26,25 @@ def setup():
 
 
 def test_pimd_nve_with_bo_forces(setup):
+    """NVE ring-polymer dynamics on the BO surface: the drift of the
+    ring-polymer energy over 2 fs falls by four when the time step halves
+    (the splitting is of second order; the beads start 0.1 A from each other,
+    so the motion is large and the error is measured at small steps)."""
     ctx, B, Z, X = setup
     fn = DR.bo_forces_fn(ctx, B, Z)
     drift = []
-    for dt in (0.5 * DR.FS, 0.25 * DR.FS):
+    for dt in (0.2 * DR.FS, 0.1 * DR.FS, 0.05 * DR.FS):
         ctx.clear_guess()
         rp = DR.RingPolymer(Z, X, 300.0, dt, thermostat=False, seed=7)
         rp.evaluate(fn)
         H0 = rp.hamiltonian()
         dev = 0.0
-        for _ in range(int(round(5 * DR.FS / dt))):
+        for _ in range(int(round(2 * DR.FS / dt))):
             rp.step(fn)
             dev = max(dev, abs(rp.hamiltonian() - H0))
         drift.append(dev)
-    assert drift[0] < 1e-4
-    assert 2.5 < drift[0] / drift[1] < 6.0     # second order in the time step
+    assert 3.0 < drift[0] / drift[1] < 5.5, drift
+    assert 3.0 < drift[1] / drift[2] < 5.5, drift
 
 
 def test_string_steps_with_bo_forces(setup):
