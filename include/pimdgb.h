@@ -93,6 +93,20 @@ typedef struct {
                              2 C_occ C_occ^T of the cached MOs; 1 that density after two McWeeny
                              purification steps in the new overlap metric; 2 the aufbau density of
                              the cached Fock matrix diagonalised in the new orthogonal basis */
+    /* Force-parallel split (the paper's force groups, Sec. 2: the integral
+     * work of every replica shared by m processes): split_size = m > 1
+     * processes call the same forces entry point with the same replicas and
+     * options except split_rank (0..m-1); each evaluates every m-th quartet
+     * tile of each class pair and after every Fock build, and after the
+     * two-electron gradient, calls reduce_fn(buf, n, reduce_user) on the host
+     * (the stream synchronised), which must replace the n doubles of the
+     * DEVICE buffer buf by their sum over the m processes (an all-reduce,
+     * e.g. NCCL) and return 0; all processes then take the same SCF path.
+     * CUDA graphs still apply to the other kernel sequences of an iteration. */
+    int split_size;       /* 1 */
+    int split_rank;       /* 0 */
+    int (*reduce_fn)(double* buf, long long n, void* user);
+    void* reduce_user;
 } pimd_scf_opts;
 
 /* Per-replica result record. */

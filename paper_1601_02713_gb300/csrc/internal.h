@@ -129,14 +129,16 @@ void launch_orth_from_eig(const RepMat* rm, int nrep, const double* U, const dou
 void launch_scale_cols(const RepMat* rm, int nrep, const double* C, const double* evals, int ldE, double* out,
                        const int* mask, cudaStream_t st);
 // DIIS
+// (stride: elements between one replica's history matrices, maxN^2)
 void launch_diis_store(const RepMat* rm, int nrep, const double* F, const double* E, double* Fh, double* Eh,
-                       const int* slot, int hist, const int* active, cudaStream_t st);
+                       const int* slot, int hist, long long stride, const int* active, cudaStream_t st);
 void launch_diis_dots(const RepMat* rm, int nrep, const double* Eh, const int* slot, const int* count, int hist,
-                      double* B, const int* active, cudaStream_t st);
+                      long long stride, double* B, const int* active, cudaStream_t st);
 void launch_diis_solve(int nrep, const double* B, const int* slot, const int* count, int hist, double* coef,
                        const int* active, cudaStream_t st);
 void launch_diis_combine(const RepMat* rm, int nrep, const double* Fh, const double* coef, int hist,
-                         const double* F, double* Fbar, const int* diis_on, const int* active, cudaStream_t st);
+                         long long stride, const double* F, double* Fbar, const int* diis_on, const int* active,
+                         cudaStream_t st);
 void launch_copy_mats(const RepMat* rm, int nrep, const double* src, double* dst, const int* mask,
                       cudaStream_t st);
 void launch_identity(const RepMat* rm, int nrep, double* A, const int* mask, cudaStream_t st);
@@ -144,7 +146,6 @@ void launch_boys_eval(int n, int m, const double* T, double* F, const double* bo
 void launch_boys_eval_f32(int n, int m, const float* T, float* F, const float* boysf, int variant, cudaStream_t st);
 void gather_xyz(const double* atom_xyz, const int* shell_atom, int nshell, double* shell_xyz, cudaStream_t st);
 void add_mats(const RepMat* rm, int nrep, const double* A, const double* B, double* C, cudaStream_t st);
-void diis_set_stride(long long stride);
 // shell-pair bounds Dsh[r][a][b] = max |M_mn| over the block (replicas in mask)
 void launch_shell_bounds(const Shells& S, const Reps& R, int nrep, int maxsh, const double* M, double* Dsh,
                          const int* mask, cudaStream_t st);

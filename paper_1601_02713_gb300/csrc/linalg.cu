@@ -538,7 +538,6 @@ __global__ void delta_density_kernel(const RepMat* rms, const double* D, double*
 
 }  // namespace
 
-static long long g_diis_stride = 0;
 
 void launch_shell_bounds(const Shells& S, const Reps& R, int nrep, int maxsh, const double* M, double* Dsh,
                          const int* mask, cudaStream_t st)
@@ -694,18 +693,17 @@ void launch_place_blocks(const RepMat* rm, const int* desc4, int nblk, const dou
     if (nblk > 0) place_blocks_kernel<<<nblk, 128, 0, st>>>(rm, desc4, nblk, src, D);
 }
 
-void diis_set_stride(long long stride) { g_diis_stride = stride; }
 
 void launch_diis_store(const RepMat* rm, int nrep, const double* F, const double* E, double* Fh, double* Eh,
-                       const int* slot, int hist, const int* active, cudaStream_t st)
+                       const int* slot, int hist, long long stride, const int* active, cudaStream_t st)
 {
-    diis_store_kernel<<<elem_grid(nrep), 256, 0, st>>>(rm, F, E, Fh, Eh, slot, hist, g_diis_stride, active);
+    diis_store_kernel<<<elem_grid(nrep), 256, 0, st>>>(rm, F, E, Fh, Eh, slot, hist, stride, active);
 }
 
 void launch_diis_dots(const RepMat* rm, int nrep, const double* Eh, const int* slot, const int* count, int hist,
-                      double* B, const int* active, cudaStream_t st)
+                      long long stride, double* B, const int* active, cudaStream_t st)
 {
-    diis_dots_kernel<<<dim3(hist, nrep), 256, 0, st>>>(rm, Eh, slot, count, hist, g_diis_stride, B, active);
+    diis_dots_kernel<<<dim3(hist, nrep), 256, 0, st>>>(rm, Eh, slot, count, hist, stride, B, active);
 }
 
 void launch_diis_solve(int nrep, const double* B, const int* slot, const int* count, int hist, double* coef,
@@ -715,9 +713,10 @@ void launch_diis_solve(int nrep, const double* B, const int* slot, const int* co
 }
 
 void launch_diis_combine(const RepMat* rm, int nrep, const double* Fh, const double* coef, int hist,
-                         const double* F, double* Fbar, const int* diis_on, const int* active, cudaStream_t st)
+                         long long stride, const double* F, double* Fbar, const int* diis_on, const int* active,
+                         cudaStream_t st)
 {
-    diis_combine_kernel<<<elem_grid(nrep), 256, 0, st>>>(rm, Fh, coef, hist, g_diis_stride, F, Fbar, diis_on,
+    diis_combine_kernel<<<elem_grid(nrep), 256, 0, st>>>(rm, Fh, coef, hist, stride, F, Fbar, diis_on,
                                                          active);
 }
 

@@ -193,6 +193,10 @@ extern "C" void pimd_scf_opts_default(pimd_scf_opts* o)
     o->full_every = 8;
     o->prim_screen = 1.0 / 81.0;
     o->reuse_mode = 0;
+    o->split_size = 1;
+    o->split_rank = 0;
+    o->reduce_fn = nullptr;
+    o->reduce_user = nullptr;
 }
 
 extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
@@ -436,7 +440,7 @@ static int class_pair_index(int X, int Y)
 
 // validate and lay out replicas; coordinates already on the device (d_xyz)
 static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, const int* Zc, const double* d_xyz,
-                       const pimd_basis* basis, double tau)
+                       const pimd_basis* basis, double tau, int split_size = 1, int split_rank = 0)
 {
     bt.nrep = nrep;
     bt.natom.assign(natom_of, natom_of + nrep);
@@ -698,6 +702,16 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
             }
             bt.nquart += bt.nq_cp[cp];
         }
+    if (split_size > 1) {
+        // force-parallel split of every replica over split_size processes: this
+        // process keeps every split_size-th tile of each class pair (the counts
+        // above stay those of the whole batch)
+        for (int cp = 0; cp < ncp; cp++) {
+            std::vector<Tile> mine;
+            for (size_t i = split_rank; i < bt.tiles[cp].size(); i += split_size) mine.push_back(bt.tiles[cp][i]);
+            bt.tiles[cp].swap(mine);
+        }
+    }
     bt.d_tiles.assign(ncp, nullptr);
     for (int cp = 0; cp < ncp; cp++) {
         if (bt.tiles[cp].empty()) continue;
@@ -718,6 +732,7 @@ struct Mats {
     double *Dp, *dD;
     int *slot, *count, *diis_on, *active, *fin, *mode;
     int* jnc;   // per replica: the eigensolver hit its sweep limit in this call
+    long long stride = 0;   // elements between one replica's DIIS history matrices
     RepMat* rm;
     int ldE;
 };
@@ -766,7 +781,7 @@ static int alloc_mats(pimd_ctx* ctx, Batch& bt, Mats& m, int hist)
     std::vector<RepMat> rm(bt.nrep);
     for (int r = 0; r < bt.nrep; r++) rm[r] = RepMat{bt.nbf[r], bt.nocc[r], bt.moff[r]};
     UPLOAD("rm", rm, m.rm);
-    diis_set_stride(stride);
+    m.stride = stride;
     return PIMD_OK;
 }
 
@@ -1124,7 +1139,9 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         for (int r = 0; r < nrep; r++) natot += natom_of[r];
         if ((rc = sad_ensure(ctx, basis, Zc, natot))) return rc;
     }
-    rc = setup_batch(ctx, bt, nrep, natom_of, Zc, d_xyz, basis, o->schwarz_tau);
+    const bool split = o->split_size > 1;
+    rc = setup_batch(ctx, bt, nrep, natom_of, Zc, d_xyz, basis, o->schwarz_tau, split ? o->split_size : 1,
+                     split ? o->split_rank : 0);
     if (rc) return rc;
     const int hist = std::max(2, std::min(16, o->diis_size));
     Mats m;
@@ -1252,6 +1269,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         float* Mf;
         ENSURE("Mf", bt.mtot, Mf);   // allocated before any capture
     }
+    double* Gsum = nullptr;   // force-split mode: G' summed over the processes
+    if (split) ENSURE("Gsum", bt.mtot, Gsum);
     int *d_mode, *d_slot, *d_count, *d_on;
     ENSURE("mode", nrep, d_mode);
     ENSURE("slot", nrep, d_slot);
@@ -1270,8 +1289,16 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         if (rc) return rc;
         CK(cudaEventRecord(ctx->ev[3], ctx->stream));
         ctx->stats.fock_builds++;
+        if (split) {
+            // this process's share of G' plus the others': the caller's sum
+            // over the split_size processes (host callback between launches)
+            CK(cudaMemcpyAsync(Gsum, m.G, sizeof(double) * bt.mtot, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (o->reduce_fn(Gsum, bt.mtot, o->reduce_user) != 0)
+                return set_err(ctx, PIMD_ECUDA, "force-split reduction of the Fock matrix failed");
+        }
         rc = run_seg(ctx, seg_err, graphs, [&]() -> int {
-            launch_fock_assemble(m.rm, nrep, m.H, m.G, m.F, m.active, ctx->stream);
+            launch_fock_assemble(m.rm, nrep, m.H, split ? Gsum : m.G, m.F, m.active, ctx->stream);
             launch_energy(m.rm, nrep, m.D, m.H, m.F, m.enn, m.E, m.active, ctx->stream);
             gemm(ctx, plan.FD, m.active);
             gemm(ctx, plan.FDS, m.active);
@@ -1342,10 +1369,10 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         UPLOAD("count", count, d_count);
         UPLOAD("diis_on", diis_on, d_on);
         rc = run_seg(ctx, seg_diag, graphs, [&]() -> int {
-            launch_diis_store(m.rm, nrep, m.F, m.M2, m.Fh, m.Eh, d_slot, hist, m.active, ctx->stream);
-            launch_diis_dots(m.rm, nrep, m.Eh, d_slot, d_count, hist, m.Bd, m.active, ctx->stream);
+            launch_diis_store(m.rm, nrep, m.F, m.M2, m.Fh, m.Eh, d_slot, hist, m.stride, m.active, ctx->stream);
+            launch_diis_dots(m.rm, nrep, m.Eh, d_slot, d_count, hist, m.stride, m.Bd, m.active, ctx->stream);
             launch_diis_solve(nrep, m.Bd, d_slot, d_count, hist, m.coef, m.active, ctx->stream);
-            launch_diis_combine(m.rm, nrep, m.Fh, m.coef, hist, m.F, m.Fb, d_on, m.active, ctx->stream);
+            launch_diis_combine(m.rm, nrep, m.Fh, m.coef, hist, m.stride, m.F, m.Fb, d_on, m.active, ctx->stream);
             ctx->stats.kernel_launches += 4;
             diag_density(ctx, bt, m, plan, m.active);
             return PIMD_OK;
@@ -1359,8 +1386,10 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     if (o->want_gradient && d_grad) {
         const int natot = bt.atom0[nrep];
         CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * natot * 3, ctx->stream));
-        launch_grad_1e(bt.P, bt.S, bt.B, bt.At, bt.R, m.D, m.W, d_grad, ctx->boys, fx_grad, ctx->stream);
-        {
+        // force-split mode: the one-electron and nuclear parts on process 0 only
+        // (the sum over the processes adds every part once)
+        if (!split || o->split_rank == 0) {
+            launch_grad_1e(bt.P, bt.S, bt.B, bt.At, bt.R, m.D, m.W, d_grad, ctx->boys, fx_grad, ctx->stream);
             int* d_ar = (int*)ctx->bufs["atom_rep2"].p;
             double* d_dummy;
             ENSURE("enn_dummy", nrep, d_dummy);
@@ -1379,6 +1408,11 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
         if (fx_grad > 0) launch_fixed_to_double(d_grad, natot * 3, fx_grad, ctx->stream);
         ctx->stats.kernel_launches += fx_grad > 0 ? 4 : 3;
+        if (split) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (o->reduce_fn(d_grad, (long long)natot * 3, o->reduce_user) != 0)
+                return set_err(ctx, PIMD_ECUDA, "force-split reduction of the gradient failed");
+        }
     }
     // MO cache (and the final Fock matrix)
     for (int r = 0; r < nrep; r++) {
@@ -1466,7 +1500,8 @@ static int check_common(pimd_ctx* ctx, const pimd_basis* basis, const pimd_scf_o
     }
     if (!(o.conv_energy > 0) || !(o.conv_error > 0) || o.max_iter < 1 || o.max_iter > 10000 ||
         !(o.schwarz_tau >= 0) || o.guess < 0 || o.guess > 5 || o.full_every < 0 || !(o.prim_screen >= 0) ||
-        o.prim_screen > 1.0 || o.reuse_mode < 0 || o.reuse_mode > 2 || o.diis_size > 16)
+        o.prim_screen > 1.0 || o.reuse_mode < 0 || o.reuse_mode > 2 || o.diis_size > 16 || o.split_size < 0 ||
+        (o.split_size > 1 && (o.split_rank < 0 || o.split_rank >= o.split_size || !o.reduce_fn)))
         return set_err(ctx, PIMD_EINVAL, "bad SCF options");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return PIMD_ECUDA;
     return PIMD_OK;

@@ -17,12 +17,18 @@ from .build import LIB
 PIMD_OK, PIMD_EINVAL, PIMD_ENOMEM, PIMD_ECUDA, PIMD_ENOTCONV, PIMD_ETIMEOUT, PIMD_EBASIS = 0, -1, -2, -3, -4, -5, -6
 
 
+# reduce_fn of the force-parallel split: int fn(double* buf, long long n, void* user)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p)
+
+
 class PimdScfOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("conv_energy", ctypes.c_double),
                 ("conv_error", ctypes.c_double), ("max_iter", ctypes.c_int), ("diis_size", ctypes.c_int),
                 ("schwarz_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("guess", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("want_gradient", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("full_every", ctypes.c_int), ("prim_screen", ctypes.c_double), ("reuse_mode", ctypes.c_int)]
+                ("full_every", ctypes.c_int), ("prim_screen", ctypes.c_double), ("reuse_mode", ctypes.c_int),
+                ("split_size", ctypes.c_int), ("split_rank", ctypes.c_int), ("reduce_fn", REDUCE_FN),
+                ("reduce_user", ctypes.c_void_p)]
 
 
 class PimdInfo(ctypes.Structure):
@@ -145,11 +151,23 @@ def _check(rc, what, allow_notconv=False, ctx=None):
 
 
 def scf_opts(**kw) -> PimdScfOpts:
-    """Defaults of pimd_scf_opts_default, overridden by keyword."""
+    """Defaults of pimd_scf_opts_default, overridden by keyword. For the
+    force-parallel split pass reduce=<python function (ptr, n) -> None> (it
+    is wrapped as reduce_fn and kept alive with the options)."""
     o = PimdScfOpts()
     load().pimd_scf_opts_default(ctypes.byref(o))
+    reduce = kw.pop("reduce", None)
     for k, v in kw.items():
         setattr(o, k, v)
+    if reduce is not None:
+        def _cb(ptr, n, user):
+            try:
+                reduce(int(ptr), int(n))
+                return 0
+            except Exception:   # an error must reach the library as a status, not unwind through C
+                return 1
+        o._reduce_cb = REDUCE_FN(_cb)
+        o.reduce_fn = o._reduce_cb
     return o
 
 

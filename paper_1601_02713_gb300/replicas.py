@@ -126,3 +126,74 @@ def distributed_step(forces_fn, Z_list, coords_list, rank: int, world: int, dist
         E_loc, G_loc = np.zeros(0), np.zeros((0, 3))
     E, G = gather_results(E_loc, G_loc, blocks, atoms, dist, device)
     return E, G, blocks
+
+
+# ---------------------------------------------------------------------------
+# Force-parallel split of each replica (the paper's force groups, Sec. 2):
+# m processes share every replica's quartet tiles and sum their partial Fock
+# matrices (and two-electron gradients) after every build. The library calls
+# a reduce function with a device buffer; these build one.
+# ---------------------------------------------------------------------------
+class _DeviceView:
+    """A float64 device buffer (address, length) as a CUDA array interface,
+    so that torch can view it without a copy."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr: int, n: int):
+    import torch
+    return torch.as_tensor(_DeviceView(ptr, n), device="cuda")
+
+
+def host_view(ptr: int, n: int):
+    """A float64 host buffer (address, length) as a torch tensor (no copy)."""
+    import ctypes
+    import torch
+    a = np.ctypeslib.as_array(ctypes.cast(int(ptr), ctypes.POINTER(ctypes.c_double)), shape=(int(n),))
+    return torch.from_numpy(a)
+
+
+def allreduce_fn(dist, group=None, host=False):
+    """reduce function for native.scf_opts(split_size=m, split_rank=r,
+    reduce=...): an in-place all-reduce (sum) of the library's device buffer
+    over the process group (NCCL), finished before it returns. host=True
+    treats the address as host memory (gloo process groups)."""
+    import torch
+
+    def fn(ptr, n):
+        t = host_view(ptr, n) if host else device_view(ptr, n)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        if not host:
+            torch.cuda.synchronize()
+    return fn
+
+
+class ThreadSum:
+    """reduce functions for m host threads that share one GPU (one context
+    each): every call deposits a host copy of its buffer, waits for the
+    others (a host barrier; no kernel waits on another) and writes the sum
+    back. The threads must make their calls in the same order."""
+
+    def __init__(self, m: int, timeout: float = 300.0):
+        import threading
+        self.m = m
+        # a thread that left its forces call (an error) breaks the barrier
+        # after the timeout instead of leaving the others waiting
+        self.bar = threading.Barrier(m, timeout=timeout)
+        self.parts = [None] * m
+
+    def fn(self, rank: int):
+        import torch
+
+        def f(ptr, n):
+            t = device_view(ptr, n)
+            self.parts[rank] = t.cpu()
+            self.bar.wait()
+            total = sum(self.parts[1:], self.parts[0].clone())
+            self.bar.wait()
+            t.copy_(total.to(t.device))
+            torch.cuda.synchronize()
+        return f

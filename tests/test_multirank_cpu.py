@@ -134,3 +134,49 @@ def test_balanced_blocks_is_the_best_contiguous_split(seed):
         edges = (0,) + cuts + (n,)
         best = min(best, max(costs[edges[i]:edges[i + 1]].sum() for i in range(world)))
     assert max(RP.block_costs(costs, blocks)) == pytest.approx(best)
+
+
+def _split_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    from paper_1601_02713_gb300 import native
+    from paper_1601_02713_gb300 import replicas as rp
+    o = native.scf_opts(split_size=world, split_rank=rank, reduce=rp.allreduce_fn(dist, host=True))
+    buf = np.arange(6, dtype=np.float64) * (rank + 1)
+    # the library's call: reduce_fn(buffer address, length, user)
+    rc = o.reduce_fn(buf.ctypes.data, len(buf), None)
+    q.put((rank, rc, buf.tolist(), o.split_size, o.split_rank))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_force_split_reduce_callback_over_gloo():
+    """The reduce function of the force-parallel split, called through the
+    C function pointer the library receives: every rank's buffer becomes the
+    sum over the ranks (here host buffers and gloo; NCCL and device buffers
+    on GPUs)."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_split_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict((r, rest) for r, *rest in (q.get(timeout=120) for _ in range(world)))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank in range(world):
+        rc, buf, size, r = res[rank]
+        assert rc == 0 and size == world and r == rank
+        np.testing.assert_array_equal(buf, np.arange(6) * 3.0)
+
+
+def test_reduce_callback_reports_errors():
+    from paper_1601_02713_gb300 import native
+
+    def bad(ptr, n):
+        raise RuntimeError("peer lost")
+    o = native.scf_opts(split_size=2, split_rank=0, reduce=bad)
+    buf = np.zeros(3)
+    assert o.reduce_fn(buf.ctypes.data, 3, None) == 1
