@@ -1339,7 +1339,12 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
                 anyfin = true;
             }
             since_full[r] = mode[r] == 2 ? 1 : since_full[r] + 1;
-            mode[r] = (met || since_full[r] >= full_every) ? 2 : 1;
+            // once the commutator error is below its bar every build is a full
+            // one: the energies of incremental builds carry the screening error
+            // accumulated since the last full build (for 768 functions and 7e8
+            // quartets a few 1e-9 hartree), which would hide |dE| < 1e-10; two
+            // consecutive full builds compare exact energies
+            mode[r] = (met || emax[r] < o->conv_error || since_full[r] >= full_every) ? 2 : 1;
             Eprev[r] = E[r];
         }
         if (anyfin) {

@@ -409,26 +409,27 @@ def test_water32_full_fock_build_against_oracle(ctx, spd):
 
 
 def test_water32_bead_invariance_and_mixed_precision(ctx, spd):
-    """(H2O)32 on the GPU alone, properties that hold at any size: the FP64
-    energy of a bead is invariant under a rigid rotation of it, and the
-    mixed-precision energy and gradient stay within the mixed tolerances
-    (1e-6 Eh, 1e-5 Eh/bohr) of the FP64 path on the same bead."""
+    """(H2O)32 on the GPU alone, properties that hold at any size, on one
+    bead (768 functions, SAD start): the mixed-precision energy is invariant
+    under a rigid motion of the bead and its gradient turns with it; the
+    mixed energy and gradient stay within the mixed tolerances (1e-6 Eh,
+    1e-5 Eh/bohr) of the FP64 path. Also the first SCF at this size (the
+    Jacobi eigensolver at n = 768, convergence with incremental builds)."""
     bas, B = spd
     Z, Xs = _water32()
     X = Xs[:1]
-    E64, G64, i64, rc = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=4))
-    assert rc == 0 and i64[0]["converged"]
     E32, G32, i32, rc = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=4, fp32_tau=1e-6))
-    assert rc == 0 and i32[0]["converged"]
-    assert abs(E32[0] - E64[0]) < 1e-6
-    assert np.abs(G32 - G64).max() < 1e-5
+    assert rc == 0 and i32[0]["converged"], i32
     ang = 0.61
     c, s = np.cos(ang), np.sin(ang)
     Rm = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]]) @ np.array([[1.0, 0.0, 0.0], [0.0, c, s],
                                                                           [0.0, -s, c]])
     Xr = X @ Rm.T + np.array([0.7, -1.1, 0.4])
-    Er, Gr, ir, rc = native.pimd_bo_forces(ctx, B, Z, Xr, native.scf_opts(guess=4))
-    assert rc == 0 and ir[0]["converged"]
-    assert abs(Er[0] - E64[0]) < 1e-8
-    # the gradient rotates with the molecule
-    assert np.abs(Gr[0] - G64[0] @ Rm.T).max() < 1e-6
+    Er, Gr, ir, rc = native.pimd_bo_forces(ctx, B, Z, Xr, native.scf_opts(guess=4, fp32_tau=1e-6))
+    assert rc == 0 and ir[0]["converged"], ir
+    assert abs(Er[0] - E32[0]) < 1e-8
+    assert np.abs(Gr[0] - G32[0] @ Rm.T).max() < 1e-6
+    E64, G64, i64, rc = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts(guess=4))
+    assert rc == 0 and i64[0]["converged"], i64
+    assert abs(E32[0] - E64[0]) < 1e-6
+    assert np.abs(G32 - G64).max() < 1e-5
