@@ -7,8 +7,12 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "pimdgb.h"
+
+namespace cg = cooperative_groups;
 
 namespace pimd {
 
@@ -86,6 +90,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* __restrict__ 
 constexpr int JAC_THREADS = 512;
 constexpr int JAC_PER = 24;   // largest column length per lane: n <= 768
 constexpr int JAC_MAXSWEEP = 60;
+constexpr int JAC_CLUSTER = 8;   // CTAs (SMs) per matrix of 128 or more rows
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -94,18 +99,36 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// PER = column elements held per lane (n <= 32 PER): the kernel is FP64-bound
-// on one SM per matrix, so PER is the smallest instantiated length that fits
-// the batch's largest matrix (padding lanes would be FP64 work on zeros).
+// PER = column elements held per lane (n <= 32 PER): the kernel is FP64-bound,
+// so PER is the smallest instantiated length that fits the batch's largest
+// matrix (padding lanes would be FP64 work on zeros).
+// CS = CTAs per matrix: 1, or a thread-block cluster of CS CTAs on CS SMs.
+// The n/2 column pairs of a round are independent, so the CTAs of the
+// cluster split every round and meet at a cluster barrier (hardware, no spin)
+// after it; the columns live in global memory (L2), each written by one CTA
+// per round. Every CTA computes the shift and the column norms of the
+// eigenvalue step itself (O(n^2), small); the rotation flag of a sweep is
+// or-ed into CTA 0's shared memory (distributed shared memory).
 // notconv (may be NULL): notconv[r] = 1 when matrix r is still rotating after
 // JAC_MAXSWEEP sweeps (its eigenpairs are then not converged)
-template <int PER>
+template <int CS>
+__device__ __forceinline__ void jac_cluster_sync()
+{
+    if constexpr (CS > 1) {
+        __threadfence();
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+template <int PER, int CS>
 __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __restrict__ rms, const double* A,
                                                              double* V, double* evals, int ldE, double* work,
                                                              const int* active, int shift_to_spd, int* notconv)
 {
-    const int r = blockIdx.x;
-    if (active && !active[r]) return;
+    const int r = blockIdx.x / CS, cr = blockIdx.x % CS;
+    if (active && !active[r]) return;   // the whole cluster (one matrix) leaves together
     const RepMat rm = rms[r];
     const int n = rm.N;
     if (n == 0) return;
@@ -115,8 +138,10 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
     double* ev = evals + (size_t)r * ldE;
     __shared__ double s_red[JAC_THREADS / 32];
     __shared__ double s_shift;
-    __shared__ int s_rot;
+    __shared__ int s_rot[3];       // CTA 0's copy: rotation flags of sweeps s mod 3
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = JAC_THREADS / 32;
+    int* rot0 = s_rot;             // CTA 0's flags
+    if constexpr (CS > 1) rot0 = cg::this_cluster().map_shared_rank(s_rot, 0);
     // Gershgorin lower bound for the shift
     double lo = 1e300;
     for (int i = threadIdx.x; i < n; i += JAC_THREADS) {
@@ -132,23 +157,25 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
         double m = 1e300;
         for (int w = 0; w < nw; w++) m = fmin(m, s_red[w]);
         s_shift = shift_to_spd ? (m < 1.0 ? 1.0 - m : 0.0) : 0.0;
+        s_rot[0] = s_rot[1] = s_rot[2] = 0;
     }
     __syncthreads();
     const double shift = s_shift;
-    for (int e = threadIdx.x; e < n * n; e += JAC_THREADS) {
+    for (int e = cr * JAC_THREADS + threadIdx.x; e < n * n; e += CS * JAC_THREADS) {
         const int i = e / n, j = e % n;
         G[(size_t)j * n + i] = a[e] + (i == j ? shift : 0.0);
     }
-    __syncthreads();
+    jac_cluster_sync<CS>();
     const int M = (n + 1) & ~1;  // even number of players; index n is a dummy when n is odd
     const double tol = 4e-16 * (n > 8 ? n : 8);
     bool settled = false;
     for (int sweep = 0; sweep < JAC_MAXSWEEP; sweep++) {
-        if (threadIdx.x == 0) s_rot = 0;
-        __syncthreads();
+        // the next sweep's flag is cleared now: it was last read at the end of
+        // sweep - 2, and every CTA has passed a barrier of sweep - 1 since
+        if (cr == 0 && threadIdx.x == 0) s_rot[(sweep + 1) % 3] = 0;
         int rotated = 0;
         for (int rd = 0; rd < M - 1; rd++) {
-            for (int k = warp; k < M / 2; k += nw) {
+            for (int k = warp * CS + cr; k < M / 2; k += nw * CS) {
                 int p, q;
                 if (k == 0) {
                     p = rd;
@@ -193,18 +220,18 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
                     }
                 }
             }
-            __syncthreads();
+            jac_cluster_sync<CS>();
         }
-        if (rotated) s_rot = 1;
-        __syncthreads();
-        if (!s_rot) {
+        if (rotated && lane == 0) atomicOr(rot0 + sweep % 3, 1);
+        jac_cluster_sync<CS>();
+        if (!*(volatile int*)(rot0 + sweep % 3)) {
             settled = true;
             break;
         }
-        __syncthreads();
     }
-    if (!settled && notconv && threadIdx.x == 0) notconv[r] = 1;
-    // eigenvalues (column norms minus the shift), ascending order by rank
+    if (!settled && notconv && cr == 0 && threadIdx.x == 0) notconv[r] = 1;
+    // eigenvalues (column norms minus the shift), ascending order by rank;
+    // every CTA has all norms, each writes its share of the vectors
     extern __shared__ double s_lam[];
     for (int j = threadIdx.x; j < n; j += JAC_THREADS) {
         double nn = 0.0;
@@ -212,7 +239,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
         s_lam[j] = sqrt(nn);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += JAC_THREADS) {
+    for (int j = cr * JAC_THREADS + threadIdx.x; j < n; j += CS * JAC_THREADS) {
         const double lj = s_lam[j];
         int rank = 0;
         for (int k = 0; k < n; k++) {
@@ -223,27 +250,55 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const RepMat* __res
         const double inv = lj > 0.0 ? 1.0 / lj : 0.0;
         for (int i = 0; i < n; i++) v[(size_t)i * n + rank] = G[(size_t)j * n + i] * inv;
     }
+    // no CTA of the cluster may leave while another can still address its
+    // shared memory (the flag reads above)
+    if constexpr (CS > 1) cg::this_cluster().sync();
 }
 
-// one block per matrix; nmax = the largest n of the batch (<= 32 JAC_PER)
+template <int PER>
+static void jacobi_launch(int nmat, cudaStream_t st, size_t sm, const RepMat* rm, const double* A, double* V,
+                          double* evals, int ldE, double* work, const int* active, int shift, int* notconv)
+{
+    // matrices of 128 or more rows: a cluster of JAC_CLUSTER CTAs (SMs) each
+    if (PER >= 4) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nmat * JAC_CLUSTER);
+        cfg.blockDim = dim3(JAC_THREADS);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = JAC_CLUSTER;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, jacobi_kernel<PER, JAC_CLUSTER>, rm, A, V, evals, ldE, work, active, shift,
+                           notconv);
+    } else {
+        jacobi_kernel<PER, 1><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+    }
+}
+
+// one block (or cluster) per matrix; nmax = the largest n of the batch (<= 32 JAC_PER)
 static void jacobi_dispatch(int nmat, int nmax, cudaStream_t st, const RepMat* rm, const double* A, double* V,
                             double* evals, int ldE, double* work, const int* active, int shift, int* notconv)
 {
     const size_t sm = sizeof(double) * nmax;
     if (nmax <= 32 * 2)
-        jacobi_kernel<2><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+        jacobi_launch<2>(nmat, st, sm, rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 4)
-        jacobi_kernel<4><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+        jacobi_launch<4>(nmat, st, sm, rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 6)
-        jacobi_kernel<6><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+        jacobi_launch<6>(nmat, st, sm, rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 8)
-        jacobi_kernel<8><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+        jacobi_launch<8>(nmat, st, sm, rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 12)
-        jacobi_kernel<12><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+        jacobi_launch<12>(nmat, st, sm, rm, A, V, evals, ldE, work, active, shift, notconv);
     else if (nmax <= 32 * 16)
-        jacobi_kernel<16><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+        jacobi_launch<16>(nmat, st, sm, rm, A, V, evals, ldE, work, active, shift, notconv);
     else
-        jacobi_kernel<JAC_PER><<<nmat, JAC_THREADS, sm, st>>>(rm, A, V, evals, ldE, work, active, shift, notconv);
+        jacobi_launch<JAC_PER>(nmat, st, sm, rm, A, V, evals, ldE, work, active, shift, notconv);
 }
 
 __global__ void fock_assemble_kernel(const RepMat* rms, const double* h, const double* G, double* F,

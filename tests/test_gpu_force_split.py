@@ -46,4 +46,6 @@ def test_two_way_split_equals_unsplit():
         assert [i["iterations"] for i in info] == [i["iterations"] for i in out[0][2]]
         np.testing.assert_allclose(E, E0, atol=1e-9, rtol=0)
         np.testing.assert_allclose(G, G0, atol=1e-8, rtol=0)
-    np.testing.assert_array_equal(out[0][0], out[1][0])
+    # the same reduced Fock matrices on both: energies agree to the last bits of
+    # the nuclear repulsion (summed with FP64 atomics in each context)
+    np.testing.assert_allclose(out[0][0], out[1][0], atol=1e-12, rtol=0)
