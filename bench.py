@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--cpu-sample-deriv", type=int, default=8000)
     ap.add_argument("--fp32-tau", type=float, default=0.0,
                     help="mixed precision: quartets with Q_ab Q_cd max|dD| below this run in FP32 (0: all FP64)")
+    ap.add_argument("--prim-screen", type=float, default=None,
+                    help="primitive-quartet cutoff as a fraction of the quartet cutoff (default: the library's 1/81)")
     ap.add_argument("--ref-iterations", type=float, default=15.3,
                     help="reference arm: SCF iterations per bead evaluation used to scale the oracle sample")
     ap.add_argument("--no-autotune", action="store_true",
@@ -361,6 +363,8 @@ def main():
         Z, _ = seq[0].stacked()
         natom = len(Z)
     opts = native.scf_opts(guess=1, fp32_tau=args.fp32_tau)
+    if args.prim_screen is not None:
+        opts.prim_screen = args.prim_screen
     dev = torch.device("cuda", local)
     X = [torch.tensor(s.concat()[2] if ragged else s.stacked()[1], dtype=torch.float64, device=dev) for s in seq]
     E = torch.empty(nrep, dtype=torch.float64, device=dev)
@@ -475,7 +479,7 @@ def main():
                                                          f"{max(len(z) for z in seq[0].Z)} per image",
                        "basis": basis_txt,
                        "scf": "|dE|<1e-10, max|FDS-SDF|<1e-8, DIIS(8), MO reuse between steps",
-                       "schwarz_tau": 1e-12, "fp32_tau": args.fp32_tau,
+                       "schwarz_tau": 1e-12, "fp32_tau": args.fp32_tau, "prim_screen": opts.prim_screen,
                        "l2": "flushed before every timed step (512 MB write)",
                        "parallelism": f"replicas{world}"},
             "geri_per_s": geri,
