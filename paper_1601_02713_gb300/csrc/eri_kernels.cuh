@@ -383,25 +383,70 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
     }
     if (threadIdx.x < PIMD_MAXPP) sqp[threadIdx.x] = P.qp[(size_t)threadIdx.x * P.n + ab];
     __syncthreads();
-    const int cd = t.c0 + threadIdx.x;
     const int r = t.rep;
-    bool work = cd < t.c1;
-    int sa = 0, sb = 0, sc = 0, sd = 0;
-    float qthr = 0.0f;
-    if (work) {
-        sa = P.sa[ab];
-        sb = P.sb[ab];
+    const int nbra = P.npp[ab];
+    // screening of ket pair c0 + k: density-weighted Schwarz bound (every
+    // contribution of the quartet to G' is at most 2 |(ab|cd)| times one of
+    // the six density blocks) and the primitive cutoff over that bound
+    auto screen = [&](int k, int& cd, int& sc, int& sd, float& qthr) -> bool {
+        cd = t.c0 + k;
+        sc = sd = 0;
+        qthr = 0.0f;
+        if (cd >= t.c1) return false;
+        const int sa = P.sa[ab], sb = P.sb[ab];
         sc = P.sa[cd];
         sd = P.sb[cd];
-        // density-weighted Schwarz bound: every contribution of the quartet to
-        // G' is at most 2 |(ab|cd)| times one of these six density blocks
         const double dq = fmax(fmax(fmax(shell_bound(R_, Dsh, r, sa, sb), shell_bound(R_, Dsh, r, sc, sd)),
                                     fmax(shell_bound(R_, Dsh, r, sa, sc), shell_bound(R_, Dsh, r, sa, sd))),
                                fmax(shell_bound(R_, Dsh, r, sb, sc), shell_bound(R_, Dsh, r, sb, sd)));
         const double bound = P.Q[ab] * P.Q[cd] * dq;
-        work = bound >= tau_lo && bound < tau_hi;
         qthr = (float)(tau_prim / dq);
+        return bound >= tau_lo && bound < tau_hi;
+    };
+    int cd, sc, sd;
+    float qthr;
+    bool work = screen(threadIdx.x, cd, sc, sd, qthr);
+    if (tau_prim > 0.0 && blockDim.x > 32) {
+        // Lanes stop their primitive loops at their own cutoff, and a warp
+        // issues for all its lanes: the block's quartets are regrouped by the
+        // number of primitive quartets that survive (descending, bitonic sort
+        // over the block), so that a warp holds quartets of similar length.
+        __shared__ int skey[128], sidx[128];
+        int est = -1;
+        if (work) {
+            est = 0;
+            const int nket = P.npp[cd];
+            for (int j = 0; j < nket; j++) {
+                const float qj = __ldg(P.qp + (size_t)j * P.n + cd);
+                int ni = 0;
+                while (ni < nbra && sqp[ni] * qj >= qthr) ni++;
+                if (ni == 0) break;
+                est += ni;
+            }
+        }
+        const int tid = threadIdx.x, bd = blockDim.x;
+        skey[tid] = est;
+        sidx[tid] = tid;
+        __syncthreads();
+        for (int k = 2; k <= bd; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int o = tid ^ j;
+                if (o > tid) {
+                    const bool desc = (tid & k) == 0;
+                    const int a = skey[tid], b = skey[o];
+                    if (desc ? a < b : a > b) {
+                        skey[tid] = b;
+                        skey[o] = a;
+                        const int x = sidx[tid];
+                        sidx[tid] = sidx[o];
+                        sidx[o] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        work = screen(sidx[tid], cd, sc, sd, qthr);
     }
+    const int sa = P.sa[ab], sb = P.sb[ab];
     // a warp with no quartet left leaves; otherwise every lane stays for the
     // warp-wide J'_ab sum (the block's warps share the bra pair)
     if (__all_sync(0xffffffffu, !work)) return;
@@ -418,7 +463,7 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        nprim = quartet_cart<C, R>(sbra, sqp, P.npp[ab], P, cd, A, B, Cc, Dd, boys, qthr, cart);
+        nprim = quartet_cart<C, R>(sbra, sqp, nbra, P, cd, A, B, Cc, Dd, boys, qthr, cart);
         cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
         f = 1.0;
         if (sa == sb) f *= 0.5;
