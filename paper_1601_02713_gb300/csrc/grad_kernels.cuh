@@ -158,13 +158,62 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
         sqg[threadIdx.x] = P.qg[(size_t)threadIdx.x * P.n + ab];
     }
     __syncthreads();
-    const int cd = t.c0 + threadIdx.x;
-    if (cd >= t.c1) return;
-    const int sa = P.sa[ab], sb = P.sb[ab], sc = P.sa[cd], sd = P.sb[cd];
-    const double gam = gamma_bound(Rp, Dsh, t.rep, sa, sb, sc, sd);
-    const double bound = P.Q[ab] * P.Q[cd] * gam;
-    if (bound < tau_lo || bound >= tau_hi) return;
-    const float gthr = (float)(tau_prim / gam);
+    const int sa = P.sa[ab], sb = P.sb[ab];
+    const int nbra = P.npp[ab];
+    // screening of ket pair c0 + k (quartet bound Q_ab Q_cd |Gamma|) and the
+    // primitive cutoff over |Gamma|
+    auto screen = [&](int k, int& cd, double& gam, float& gthr) -> bool {
+        cd = t.c0 + k;
+        gam = 0.0;
+        gthr = 0.0f;
+        if (cd >= t.c1) return false;
+        gam = gamma_bound(Rp, Dsh, t.rep, sa, sb, P.sa[cd], P.sb[cd]);
+        const double bound = P.Q[ab] * P.Q[cd] * gam;
+        gthr = (float)(tau_prim / gam);
+        return bound >= tau_lo && bound < tau_hi;
+    };
+    int cd;
+    double gam;
+    float gthr;
+    bool work = screen(threadIdx.x, cd, gam, gthr);
+    if (tau_prim > 0.0 && blockDim.x > 32) {
+        // regroup the block's quartets by their number of surviving primitive
+        // quartets (bitonic sort, descending): lanes stop at their own cutoff
+        // and a warp issues for all its lanes
+        __shared__ int skey[128], sidx[128];
+        int est = -1;
+        if (work) {
+            est = 0;
+            const int nket = P.npp[cd];
+            for (int j = 0; j < nket; j++) {
+                const float qpj = __ldg(P.qp + (size_t)j * P.n + cd), qgj = __ldg(P.qg + (size_t)j * P.n + cd);
+                for (int i = 0; i < nbra; i++) est += sqg[i] * qpj + sqp[i] * qgj >= gthr;
+            }
+        }
+        const int tid = threadIdx.x, bd = blockDim.x;
+        skey[tid] = est;
+        sidx[tid] = tid;
+        __syncthreads();
+        for (int k = 2; k <= bd; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int o = tid ^ j;
+                if (o > tid) {
+                    const bool desc = (tid & k) == 0;
+                    const int a = skey[tid], b = skey[o];
+                    if (desc ? a < b : a > b) {
+                        skey[tid] = b;
+                        skey[o] = a;
+                        const int x = sidx[tid];
+                        sidx[tid] = sidx[o];
+                        sidx[o] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        work = screen(sidx[tid], cd, gam, gthr);
+    }
+    if (!work) return;
+    const int sc = P.sa[cd], sd = P.sb[cd];
     double A[3], B[3], Cc[3], Dd[3];
 #pragma unroll
     for (int x = 0; x < 3; x++) {
@@ -178,7 +227,7 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
     for (int i = 0; i < G::N_accA; i++) accA[i] = R(0);
     for (int i = 0; i < G::N_accB; i++) accB[i] = R(0);
     for (int i = 0; i < G::N_accC; i++) accC[i] = R(0);
-    const int nbra = P.npp[ab], nket = P.npp[cd];
+    const int nket = P.npp[cd];
     for (int j = 0; j < nket; j++) {
         const float qpj = __ldg(P.qp + (size_t)j * P.n + cd), qgj = __ldg(P.qg + (size_t)j * P.n + cd);
         R ket[PP_NF];
