@@ -166,15 +166,33 @@ def job_throughput(beads_per_rank, world, steps, t_max):
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
+def oracle_whole(step_reps, kind):
+    """The oracle on every replica of the step, whole: one-electron integrals,
+    SCF to the same bars, gradient (small systems). Returns (replica evals/s,
+    threads, sample text, s)."""
+    import oracle as O
+    bas = inputs.basis_set(kind)
+    t0 = time.time()
+    for Z, X in zip(step_reps.Z, step_reps.coords):
+        O.rhf_energy_gradient(bas, Z, X)
+    dt = time.time() - t0
+    n = len(step_reps.Z)
+    return n / dt, O.num_threads(), f"every replica of the step ({n}), whole: integrals, SCF and gradient", dt
+
+
 def oracle_sample(step_reps, kind, iterations, n_eri, n_der, seed=11):
     """Time the oracle on a bounded sample of one bead of the workload:
     random screened shell quartets of bead 0 for the Fock build (n_eri) and for
     the derivative integrals (n_der); per-bead time = iterations x quartets x
-    t_eri + quartets x t_der. Returns (bead evals/s, threads, sample text, s)."""
+    t_eri + quartets x t_der. Systems of at most 64 basis functions are timed
+    whole instead (oracle_whole). Returns (bead evals/s, threads, sample
+    text, s)."""
     import oracle as O
     bas = inputs.basis_set(kind)
     Z, X = step_reps.Z[0], step_reps.coords[0]
     ob = O.OracleBasis.build(bas, Z, X)
+    if ob.nbf <= 64:
+        return oracle_whole(step_reps, kind)
     t0 = time.time()
     q = O.canonical_quartets(ob, 1e-12)
     rng = np.random.default_rng(seed)
