@@ -478,6 +478,9 @@ def main():
     geri = eris / (fock_ms * 1e-3) / 1e9
     eris32 = sum(s.get("eris32_per_build", 0.0) * s["fock_builds"] for s in stats)
     launches = int(sum(s["kernel_launches"] for s in stats))
+    grad_ms = max(sum(s["ms_grad2e"] for s in stats), 1e-9)
+    gflops = sum(s.get("grad_flops", 0.0) for s in stats)
+    gflops32 = sum(s.get("grad_flops32", 0.0) for s in stats)
 
     Bq = native.Basis(inputs.basis_set(kind))
     if ragged:
@@ -521,6 +524,16 @@ def main():
                                   "pipe (mixed mode); their sum is the share of the two pipes' peak the build uses"),
                          "flops_per_launch": flops / max(builds, 1), "ms_per_launch": fock_ms / max(builds, 1),
                          "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (FMA chain measured 1.255)"},
+            "grad_roofline": {"kernel": "grad2e_kernel / grad2e_coop_kernel (all quartet classes, one per "
+                                        "forces call)", "bound": "alu",
+                              "achieved": gflops / (grad_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": gflops / (grad_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                              "fp32_achieved": gflops32 / (grad_ms * 1e-3) / 1e12,
+                              "fp32_frac": gflops32 / (grad_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                              "flops_per_step": gflops / K, "ms_per_step": grad_ms / K,
+                              "note": ("per executed primitive quartet: the generated recursion to order L + 1 with "
+                                       "its four accumulated sets, set-up and Boys; the HRRs, the density "
+                                       "contraction and the Cartesian/spherical transforms are not counted")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(coord_bytes),
                     "d2h_bytes_per_step": int(nrep * 8 + coord_bytes)},
             "gpu_launches": launches,

@@ -85,10 +85,11 @@ typedef struct {
                              qp_ij qp_kl max|D block| (qp: Schwarz factor of one primitive pair) is
                              below schwarz_tau * prim_screen are skipped in the Fock build (at most
                              81 per quartet, so their sum stays below schwarz_tau); in the gradient,
-                             whose quartets are screened at schwarz_tau / 100 on Q_ab Q_cd |Gamma|, a
-                             primitive quartet is skipped below schwarz_tau / 100 * prim_screen with
-                             the derivative-scaled bound (qg_ij qp_kl + qp_ij qg_kl) |Gamma|, qg =
-                             qp 2 sqrt(2 max exponent); 0 keeps all */
+                             whose quartets are screened at schwarz_tau / 100 on Q_ab Q_cd |Gamma|
+                             (Q carries no derivative scale, hence the margin), a primitive quartet
+                             is skipped below schwarz_tau * prim_screen with the derivative bound
+                             (qg_ij qp_kl + qp_ij qg_kl) |Gamma|, qg = qp 2 sqrt(2 max exponent),
+                             which carries that scale itself; 0 keeps all */
     int reuse_mode;       /* start of a replica from its previous call (guess 1, 3, 5): 0 the density
                              2 C_occ C_occ^T of the cached MOs; 1 that density after two McWeeny
                              purification steps in the new overlap metric; 2 the aufbau density of
@@ -116,6 +117,8 @@ typedef struct {
     double final_dE;      /* last |E_k - E_{k-1}| */
     double final_error;   /* last max |X^T (FDS - SDF) X| */
     long long nquartets;  /* screened shell quartets per Fock build */
+    long long nq_fp64;    /* shell quartets of the replica executed in FP64, all Fock builds of the call */
+    long long nq_fp32;    /* ... and in FP32 (mixed mode: bound below fp32_tau) */
 } pimd_info;
 
 void pimd_scf_opts_default(pimd_scf_opts* opts);
@@ -203,6 +206,11 @@ typedef struct {
     long long quartets_fp64;     /* executed shell quartets of all Fock builds of the call, FP64 */
     long long quartets_fp32;     /* ... and FP32 (fp32_tau > 0) */
     double eris32_per_build;     /* the part of eris_per_build evaluated in FP32 */
+    double grad_flops;           /* executed floating-point operations of the two-electron gradient's
+                                    primitive loop in FP64 (generated recursion to order L + 1 with its
+                                    four accumulated sets, set-up and Boys), all replicas */
+    double grad_flops32;         /* the same for its FP32 quartets (mixed mode) */
+    long long grad_quartets;     /* executed shell quartets of the two-electron gradient */
 } pimd_stats;
 int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
 
@@ -212,6 +220,13 @@ int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out);
  * full_build[k] (1 full Fock build, 0 incremental). Any output may be NULL.
  * Returns the number of iterations of the replica, or a negative error. */
 int pimd_last_trace(const pimd_ctx* ctx, int rep, int maxit, double* energy, double* error, int* full_build);
+
+/* Fock builds of the last forces call, per SCF iteration k < min(returned
+ * count, maxit) (one build covers every replica still iterating): ms[k] the
+ * device time of the build (CUDA events on the context stream) and
+ * quartets[k] the shell quartets it executed (FP64 and FP32). Either output
+ * may be NULL. Returns the number of iterations, or a negative error. */
+int pimd_last_fock_times(const pimd_ctx* ctx, int maxit, double* ms, long long* quartets);
 
 /* Testing hooks (same kernels as the forces path):
  * pimd_fock_dev: for nrep replicas of one molecule and a given density

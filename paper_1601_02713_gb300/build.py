@@ -80,11 +80,12 @@ def _coop_upload_code(nm, grad, g):
              f"static void coop_tape_{nm}(CoopTape& t, int& W, size_t& bytes, int& Wf, size_t& bytesf)", "{",
              "    int dev = 0;", "    cudaGetDevice(&dev);",
              f"    const int per = coop_warp_doubles({st}::NACC, {st}::NWORK, {st}::L, {nc4});",
-             "    W = (int)(220 * 1024 / (per * sizeof(double)));",
-             "    W = W < 1 ? 1 : (W > 4 ? 4 : W);",
+             "    // warps per block (1..4, the kernels' launch bound): the count that puts",
+             "    // the most warps on an SM within its 228 KB of shared memory (227 KB",
+             "    // per block, 1 KB reserved per block); ties go to the larger block",
+             "    W = coop_best_warps((size_t)per * sizeof(double));",
              "    bytes = (size_t)W * per * sizeof(double);",
-             "    Wf = (int)(220 * 1024 / (per * sizeof(float)));",
-             "    Wf = Wf < 1 ? 1 : (Wf > 4 ? 4 : Wf);",
+             "    Wf = coop_best_warps((size_t)per * sizeof(float));",
              "    bytesf = (size_t)Wf * per * sizeof(float);",
              "    if (dev >= 0 && dev < 64 && !g_coop_up[dev]) {",
              "        CoopTape c{};",
@@ -106,6 +107,8 @@ def _coop_upload_code(nm, grad, g):
     lines += ["        g_coop[dev] = c;", "        g_coop_up[dev] = true;",
               f"        cudaFuncSetAttribute({kernel}, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);",
               f"        cudaFuncSetAttribute({kernel}, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytesf);",
+              f"        cudaFuncSetAttribute({kernel}, double>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);",
+              f"        cudaFuncSetAttribute({kernel}, float>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);",
               "    }", "    t = g_coop[dev];", "}"]
     return lines
 
@@ -187,8 +190,8 @@ def generate_sources():
         # variant 0: warp-cooperative tape kernel, 1: straight-line kernel with bs threads
         gl += [f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                "                        const double* D, double* grad, const double* boys, const float* boysf,",
-               "                        double tau, double fp32_tau, const double* Dsh, int variant, int bs,",
-               "                        double tp, double fxs, cudaStream_t st)",
+               "                        double tau, double fp32_tau, const double* Dsh, unsigned long long* cnt,",
+               "                        int variant, int bs, double tp, double fxs, cudaStream_t st)",
                "{",
                "    if (ntiles <= 0) return;",
                "    const double split = fp32_tau > tau ? fp32_tau : tau;"]
@@ -197,19 +200,19 @@ def generate_sources():
                    "        CoopTape t; int W, Wf; size_t bytes, bytesf;",
                    f"        coop_tape_{nm}(t, W, bytes, Wf, bytesf);",
                    f"        grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, double><<<ntiles, 32 * W, bytes, st>>>(P, S, R,",
-                   "            tiles, D, grad, boys, split, 1e300, Dsh, t, tp, fxs);",
+                   "            tiles, D, grad, boys, split, 1e300, Dsh, cnt, t, tp, fxs);",
                    "        if (fp32_tau > tau)",
                    f"            grad2e_coop_kernel<{la}, {lb}, {lc}, {ld}, float><<<ntiles, 32 * Wf, bytesf, st>>>(P, S,",
-                   "                R, tiles, D, grad, boysf, tau, fp32_tau, Dsh, t, tp, fxs);",
+                   "                R, tiles, D, grad, boysf, tau, fp32_tau, Dsh, cnt + 2, t, tp, fxs);",
                    "        return;",
                    "    }"]
         if not heavy[nm]:
             gl += ["    const int b = bs > 0 ? bs : 128;",
                    f"    grad2e_kernel<GCls_{nm}, double><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boys, split, 1e300, Dsh,",
-                   "                                                            tp, fxs);",
+                   "                                                            cnt, tp, fxs);",
                    "    if (fp32_tau > tau)",
                    f"        grad2e_kernel<GCls_{nm}, float><<<ntiles, b, 0, st>>>(P, S, R, tiles, D, grad, boysf, tau, fp32_tau,",
-                   "                                                           Dsh, tp, fxs);"]
+                   "                                                           Dsh, cnt + 2, tp, fxs);"]
         gl.append("}")
         gl.append("}  // namespace pimd\n")
         p = os.path.join(GEN, f"tu_grad_{nm}.cu")
@@ -223,7 +226,7 @@ def generate_sources():
     sig_sw = "const Pairs&, const Shells&, const int*, int, const double*, double*, cudaStream_t"
     sig_psw = "const Pairs&, const Shells&, const int*, int, const double*, double*, float*, float*, cudaStream_t"
     sig_g = ("const Pairs&, const Shells&, const Reps&, const Tile*, int, const double*, double*, const double*, "
-             "const float*, double, double, const double*, int, int, double, double, cudaStream_t")
+             "const float*, double, double, const double*, unsigned long long*, int, int, double, double, cudaStream_t")
     for c, nm in zip(classes, names):
         d.append(f"void launch_jk_{nm}({sig_jk});")
         if (c[0], c[1]) == (c[2], c[3]):
@@ -245,6 +248,16 @@ def generate_sources():
     # (17 for the Taylor step and prefactor; for L > 0 also 16 for e^{-T} and
     # 3 per order of the downward recursion)
     d.append("    static const long long t[] = {" + ", ".join(str(flops[nm] + 42 + (16 + 3 * sum(c) if sum(c) else 0))
+                                                        for c, nm in zip(classes, names)) + "};")
+    d.append("    return t[cp];")
+    d.append("}")
+    gflops = {s[0]: s[5] for s in stats}
+    d.append("long long class_grad_flops(int cp)")
+    d.append("{")
+    # per primitive quartet of the gradient: the generated recursion to order
+    # L + 1 with its four accumulated sets, the same set-up (42) and the Boys
+    # function to order L + 1 (16 + 3 (L + 1))
+    d.append("    static const long long t[] = {" + ", ".join(str(gflops[nm] + 42 + 16 + 3 * (sum(c) + 1))
                                                         for c, nm in zip(classes, names)) + "};")
     d.append("    return t[cp];")
     d.append("}")
@@ -278,9 +291,10 @@ def generate_sources():
 
     d.append("void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles, "
              "const double* D, double* grad, const double* boys, const float* boysf, double tau, double fp32_tau, "
-             "const double* Dsh, int variant, int bs, double tau_prim, double fxs, cudaStream_t st)")
-    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, variant, bs, tau_prim, fxs, "
-             "st); }")
+             "const double* Dsh, unsigned long long* cnt, int variant, int bs, double tau_prim, double fxs, "
+             "cudaStream_t st)")
+    d.append("{ g_tab[cp](P, S, R, tiles, ntiles, D, grad, boys, boysf, tau, fp32_tau, Dsh, cnt, variant, bs, tau_prim, "
+             "fxs, st); }")
     d.append("void grad2e_tapes_upload() {")
     for nm in names:
         d.append(f"    grad2e_upload_{nm}();")

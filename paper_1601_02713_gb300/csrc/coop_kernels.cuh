@@ -18,7 +18,7 @@ namespace pimd {
 struct CoopTape {
     const int* vrr;        // 4 ints per op (see coop_vrr), level-sorted, each level by chain length
     const int* vrr_lv;     // level offsets
-    const int* acc;        // 4 ints per op: dst, src, weight, 0
+    const int* acc;        // 1 int per op: dst | src << 14 | weight << 28 (see coop_accumulate)
     const int* hrr[6];     // HRR tapes, 2 ints per op (energy: [0] only; gradient: Ap Bp Cp Am Bm Cm)
     const int* hrr_lv[6];
     const int* out[6];     // slots of the Cartesian outputs of each HRR tape
@@ -62,24 +62,63 @@ __device__ __forceinline__ void coop_fill_ct(const R* g, R* ct, int lane)
 // run the level-sorted VRR of one primitive quartet (coefficients ct) in sm:
 // every op is sm[dst] = sum over its 2..5 terms of ct[c_t] sm[s_t], encoded
 // as {dst | s1 << 16, s2 | s3 << 16, s4 | s5 << 16, c1 | c2 << 6 | c3 << 12 |
-// c4 << 18 | c5 << 24 | (terms - 2) << 30}
+// c4 << 18 | c5 << 24 | (terms - 2) << 30}. The ops of a level are
+// independent (they read earlier levels only and write distinct slots), so a
+// lane takes two of them at a time and the loads of both overlap.
+template <typename R>
+__device__ __forceinline__ R coop_vrr_op(const int4 op, const R* sm, const R* ct)
+{
+    const unsigned w0 = (unsigned)op.x, w1 = (unsigned)op.y, w2 = (unsigned)op.z, w3 = (unsigned)op.w;
+    const unsigned n = w3 >> 30;
+    R v = ct[w3 & 63] * sm[w0 >> 16];
+    v = fma(ct[(w3 >> 6) & 63], sm[w1 & 0xffff], v);
+    if (n >= 1) v = fma(ct[(w3 >> 12) & 63], sm[w1 >> 16], v);
+    if (n >= 2) v = fma(ct[(w3 >> 18) & 63], sm[w2 & 0xffff], v);
+    if (n >= 3) v = fma(ct[(w3 >> 24) & 63], sm[w2 >> 16], v);
+    return v;
+}
+
 template <typename R>
 __device__ __forceinline__ void coop_vrr(const CoopTape& tp, R* sm, const R* ct, int lane)
 {
     for (int lv = 0; lv < tp.nvlev; lv++) {
         const int hi = __ldg(tp.vrr_lv + lv + 1);
-        for (int o = __ldg(tp.vrr_lv + lv) + lane; o < hi; o += 32) {
-            const int4 op = __ldg((const int4*)(tp.vrr + 4 * o));
-            const unsigned w0 = (unsigned)op.x, w1 = (unsigned)op.y, w2 = (unsigned)op.z, w3 = (unsigned)op.w;
-            const unsigned n = w3 >> 30;
-            R v = ct[w3 & 63] * sm[w0 >> 16];
-            v = fma(ct[(w3 >> 6) & 63], sm[w1 & 0xffff], v);
-            if (n >= 1) v = fma(ct[(w3 >> 12) & 63], sm[w1 >> 16], v);
-            if (n >= 2) v = fma(ct[(w3 >> 18) & 63], sm[w2 & 0xffff], v);
-            if (n >= 3) v = fma(ct[(w3 >> 24) & 63], sm[w2 >> 16], v);
-            sm[w0 & 0xffff] = v;
+        int o = __ldg(tp.vrr_lv + lv) + lane;
+        for (; o + 32 < hi; o += 64) {
+            const int4 a = __ldg((const int4*)(tp.vrr + 4 * o));
+            const int4 b = __ldg((const int4*)(tp.vrr + 4 * (o + 32)));
+            const R va = coop_vrr_op<R>(a, sm, ct);
+            const R vb = coop_vrr_op<R>(b, sm, ct);
+            sm[(unsigned)a.x & 0xffff] = va;
+            sm[(unsigned)b.x & 0xffff] = vb;
+        }
+        if (o < hi) {
+            const int4 a = __ldg((const int4*)(tp.vrr + 4 * o));
+            sm[(unsigned)a.x & 0xffff] = coop_vrr_op<R>(a, sm, ct);
         }
         __syncwarp();
+    }
+}
+
+// accumulation of one primitive quartet's VRR results into the contracted
+// sets: op {dst | src << 14 | weight << 28}, sm[dst] += w[weight] sm[src]
+// (w = 1, 2a, 2b, 2c); every accumulator has one op, so the ops are
+// independent and a lane takes two at a time
+template <typename R>
+__device__ __forceinline__ void coop_accumulate(const CoopTape& tp, R* sm, const R w[4], int lane)
+{
+    auto wsel = [&](unsigned k) { return k == 0 ? w[0] : (k == 1 ? w[1] : (k == 2 ? w[2] : w[3])); };
+    int o = lane;
+    for (; o + 32 < tp.naccop; o += 64) {
+        const unsigned a = (unsigned)__ldg(tp.acc + o), b = (unsigned)__ldg(tp.acc + o + 32);
+        const R va = fma(wsel(a >> 28), sm[(a >> 14) & 0x3fff], sm[a & 0x3fff]);
+        const R vb = fma(wsel(b >> 28), sm[(b >> 14) & 0x3fff], sm[b & 0x3fff]);
+        sm[a & 0x3fff] = va;
+        sm[b & 0x3fff] = vb;
+    }
+    if (o < tp.naccop) {
+        const unsigned a = (unsigned)__ldg(tp.acc + o);
+        sm[a & 0x3fff] = fma(wsel(a >> 28), sm[(a >> 14) & 0x3fff], sm[a & 0x3fff]);
     }
 }
 
@@ -90,14 +129,25 @@ __device__ __forceinline__ void coop_hrr(const CoopTape& tp, int h, R* sm, const
 {
     const int* ops = tp.hrr[h];
     const int* lvo = tp.hrr_lv[h];
+    auto coef = [&](unsigned c) {
+        return c == 0 ? hc[0] : c == 1 ? hc[1] : c == 2 ? hc[2] : c == 3 ? hc[3] : c == 4 ? hc[4] : hc[5];
+    };
     for (int lv = 0; lv < tp.nhlev[h]; lv++) {
         const int hi = __ldg(lvo + lv + 1);
-        for (int o = __ldg(lvo + lv) + lane; o < hi; o += 32) {
-            const int2 op = __ldg((const int2*)(ops + 2 * o));
-            const unsigned a = (unsigned)op.x, b = (unsigned)op.y;
-            const unsigned c = b >> 16;
-            const R coef = c == 0 ? hc[0] : c == 1 ? hc[1] : c == 2 ? hc[2] : c == 3 ? hc[3] : c == 4 ? hc[4] : hc[5];
-            sm[a & 0xffff] = fma(coef, sm[b & 0xffff], sm[a >> 16]);
+        int o = __ldg(lvo + lv) + lane;
+        // a level's ops are independent: two per lane at a time
+        for (; o + 32 < hi; o += 64) {
+            const int2 p = __ldg((const int2*)(ops + 2 * o)), q = __ldg((const int2*)(ops + 2 * (o + 32)));
+            const unsigned pa = (unsigned)p.x, pb = (unsigned)p.y, qa = (unsigned)q.x, qb = (unsigned)q.y;
+            const R vp = fma(coef(pb >> 16), sm[pb & 0xffff], sm[pa >> 16]);
+            const R vq = fma(coef(qb >> 16), sm[qb & 0xffff], sm[qa >> 16]);
+            sm[pa & 0xffff] = vp;
+            sm[qa & 0xffff] = vq;
+        }
+        if (o < hi) {
+            const int2 p = __ldg((const int2*)(ops + 2 * o));
+            const unsigned pa = (unsigned)p.x, pb = (unsigned)p.y;
+            sm[pa & 0xffff] = fma(coef(pb >> 16), sm[pb & 0xffff], sm[pa >> 16]);
         }
         __syncwarp();
     }
@@ -167,10 +217,7 @@ __device__ __forceinline__ int coop_primitive_loop(const CoopTape& tp, const Pai
             __syncwarp();
             coop_vrr<R>(tp, sm, ct, lane);
             const R w[4] = {R(1), g[17], g[18], g[19]};
-            for (int o = lane; o < tp.naccop; o += 32) {
-                const int4 a = __ldg((const int4*)(tp.acc + 4 * o));
-                sm[a.x] += (a.z == 0 ? w[0] : (a.z == 1 ? w[1] : (a.z == 2 ? w[2] : w[3]))) * sm[a.y];
-            }
+            coop_accumulate<R>(tp, sm, w, lane);
             __syncwarp();
         }
     }
@@ -294,6 +341,26 @@ __host__ __device__ constexpr int coop_warp_doubles(int NACC, int NWORK, int L, 
     return NACC + NWORK + 32 * (COOP_NG0 + L + 1) + 2 * ncart4 + COOP_CT;
 }
 
+// warps per block for a warp workspace of `per_warp` bytes: the W in 1..4 that
+// maximises W x (blocks resident per SM), the SM holding 228 KB of shared
+// memory with 1 KB reserved per block and a block at most 227 KB
+inline int coop_best_warps(size_t per_warp)
+{
+    const size_t sm_bytes = 228 * 1024, blk_max = 227 * 1024, reserve = 1024;
+    int best = 1;
+    size_t best_warps = 0;
+    for (int W = 1; W <= 4; W++) {
+        const size_t blk = (size_t)W * per_warp;
+        if (blk > blk_max) break;
+        const size_t warps = (size_t)W * (sm_bytes / (blk + reserve));
+        if (warps >= best_warps) {
+            best_warps = warps;
+            best = W;
+        }
+    }
+    return best;
+}
+
 // Fock build of the quartets whose density-weighted bound lies in [tau_lo, tau_hi)
 template <int LA, int LB, int LC, int LD, typename Rt>
 __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
@@ -338,6 +405,7 @@ __global__ void __launch_bounds__(128) jk_coop_kernel(Pairs P, Shells S, Reps R,
         if (lane == 0) {
             atomicAdd(cnt, 1ull);
             atomicAdd(cnt + 1, (unsigned long long)nprim);
+            atomicAdd(R.qrep + 2 * r + (sizeof(Rt) == 4 ? 1 : 0), 1ull);
         }
         const Rt hc[6] = {Rt(A[0] - B[0]), Rt(A[1] - B[1]), Rt(A[2] - B[2]),
                           Rt(Cc[0] - Dd[0]), Rt(Cc[1] - Dd[1]), Rt(Cc[2] - Dd[2])};
@@ -363,7 +431,8 @@ template <int LA, int LB, int LC, int LD, typename Rt>
 __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Reps R, const Tile* __restrict__ tiles,
                                                           const double* __restrict__ Dall, double* __restrict__ grad,
                                                           const Rt* __restrict__ boys, double tau_lo, double tau_hi,
-                                                          const double* __restrict__ Dsh, CoopTape tp,
+                                                          const double* __restrict__ Dsh,
+                                                          unsigned long long* __restrict__ cnt, CoopTape tp,
                                                           double tau_prim, double fxs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -397,7 +466,12 @@ __global__ void __launch_bounds__(128) grad2e_coop_kernel(Pairs P, Shells S, Rep
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, ct, lane, (float)(tau_prim / gam), true);
+        const int nprim = coop_primitive_loop<Rt>(tp, P, ab, cd, boys, sm, geom, ct, lane, (float)(tau_prim / gam),
+                                                  true);
+        if (lane == 0) {
+            atomicAdd(cnt, 1ull);
+            atomicAdd(cnt + 1, (unsigned long long)nprim);
+        }
         // Gamma: spherical, then the transpose transform to Cartesian components
         double f = 1.0;
         if (sa == sb) f *= 0.5;

@@ -321,26 +321,49 @@ __device__ __forceinline__ const float* pp_base(const Pairs& P, float) { return 
 // Primitive screening: primitive quartet (i|j) is skipped when
 // qp_i qp_j < qthr (qthr = the primitive cutoff over the quartet's density
 // bound; qthr <= 0 keeps every primitive); both primitive lists are in
-// descending order of qp, so each loop stops at its first skipped entry.
+// descending order of qp, so the quartets that survive form a staircase: for
+// ket primitive j the bra primitives i < imax(j), imax non-increasing. The
+// loop walks that staircase as one flat sequence of `total` primitive
+// quartets, and runs `kmax` iterations (kmax >= total, the longest sequence
+// of the warp), so that a warp executes the recursion once per position of
+// its longest lane instead of once per primitive quartet that any lane needs.
 // Returns the number of primitive quartets evaluated.
+__device__ __forceinline__ int stair_width(const float* sqp, int nbra, float qj, float qthr)
+{
+    int n = 0;
+    while (n < nbra && sqp[n] * qj >= qthr) n++;
+    return n;
+}
+
+__device__ __forceinline__ int stair_total(const float* sqp, int nbra, const Pairs& P, int cd, float qthr)
+{
+    const int nket = P.npp[cd];
+    if (qthr <= 0.0f) return nbra * nket;
+    int total = 0;
+    for (int j = 0; j < nket; j++) {
+        const int w = stair_width(sqp, nbra, __ldg(P.qp + (size_t)j * P.n + cd), qthr);
+        if (w == 0) break;
+        total += w;
+    }
+    return total;
+}
+
 template <class C, typename R>
 __device__ __forceinline__ int quartet_cart(const R (*sbra)[PIMD_MAXPP], const float* sqp, int nbra, const Pairs& P,
                                             int cd, const double A[3], const double B[3], const double Cc[3],
-                                            const double Dd[3], const R* __restrict__ boys, float qthr, R* cart)
+                                            const double Dd[3], const R* __restrict__ boys, float qthr, int total,
+                                            int kmax, R* cart)
 {
     R acc[C::NE * C::NF];
 #pragma unroll
     for (int i = 0; i < C::NE * C::NF; i++) acc[i] = R(0);
     const int nket = P.npp[cd];
-    int nprim = 0;
-    for (int j = 0; j < nket; j++) {
-        const float qj = qthr > 0.0f ? __ldg(P.qp + (size_t)j * P.n + cd) : 1.0f;
-        if (qj * sqp[0] < qthr) break;
-        R ket[PP_NERI];
-        load_ppn(P, cd, j, ket, PP_NERI);
-        for (int i = 0; i < nbra; i++) {
-            if (sqp[i] * qj < qthr) break;
-            nprim++;
+    int i = 0, j = 0;
+    int w = total > 0 ? (qthr > 0.0f ? stair_width(sqp, nbra, __ldg(P.qp + cd), qthr) : nbra) : 0;
+    R ket[PP_NERI];
+    for (int k = 0; k < kmax; k++) {
+        if (k < total) {
+            if (i == 0) load_ppn(P, cd, j, ket, PP_NERI);
             R bra[PP_NERI];
 #pragma unroll
             for (int f = 0; f < PP_NERI; f++) bra[f] = sbra[f][i];
@@ -350,18 +373,18 @@ __device__ __forceinline__ int quartet_cart(const R (*sbra)[PIMD_MAXPP], const f
             boys_eval<C::L>(g.T, boys, g.theta, F);
             C::template vrr<R>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1], g.QC[2],
                                g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, acc);
+            if (++i == w) {
+                i = 0;
+                if (++j < nket)
+                    w = qthr > 0.0f ? stair_width(sqp, nbra, __ldg(P.qp + (size_t)j * P.n + cd), qthr) : nbra;
+            }
         }
     }
     C::template hrr<R>(acc, R(A[0] - B[0]), R(A[1] - B[1]), R(A[2] - B[2]), R(Cc[0] - Dd[0]), R(Cc[1] - Dd[1]),
                        R(Cc[2] - Dd[2]), cart);
-    return nprim;
+    return total;
 }
 
-// Fock (G') build over the quartets of one class pair whose density-weighted
-// Schwarz bound lies in [tau_lo, tau_hi), in precision R (FP64, or FP32 for
-// the small quartets of the mixed mode). blockDim.x == the tile's ket width
-// (32, 64 or 128, chosen per class pair by the autotuner).
-// cnt: executed quartets and primitive quartets.
 // tau_prim: primitive quartets whose bound qp_i qp_j (density bound) is below
 // it are skipped (0 keeps every primitive quartet). fxs > 0: G' accumulated as
 // fixed-point integers (det_add).
@@ -412,18 +435,7 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
         // number of primitive quartets that survive (descending, bitonic sort
         // over the block), so that a warp holds quartets of similar length.
         __shared__ int skey[128], sidx[128];
-        int est = -1;
-        if (work) {
-            est = 0;
-            const int nket = P.npp[cd];
-            for (int j = 0; j < nket; j++) {
-                const float qj = __ldg(P.qp + (size_t)j * P.n + cd);
-                int ni = 0;
-                while (ni < nbra && sqp[ni] * qj >= qthr) ni++;
-                if (ni == 0) break;
-                est += ni;
-            }
-        }
+        const int est = work ? stair_total(sqp, nbra, P, cd, qthr) : -1;
         const int tid = threadIdx.x, bd = blockDim.x;
         skey[tid] = est;
         sidx[tid] = tid;
@@ -454,6 +466,8 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
     R cart[NCART], tmp[NCART];
     double f = 0.0;
     int nprim = 0;
+    const int total = work ? stair_total(sqp, nbra, P, cd, qthr) : 0;
+    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)total);
     if (work) {
         double A[3], B[3], Cc[3], Dd[3];
 #pragma unroll
@@ -463,7 +477,7 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
             Cc[x] = S.xyz[3 * sc + x];
             Dd[x] = S.xyz[3 * sd + x];
         }
-        nprim = quartet_cart<C, R>(sbra, sqp, nbra, P, cd, A, B, Cc, Dd, boys, qthr, cart);
+        nprim = quartet_cart<C, R>(sbra, sqp, nbra, P, cd, A, B, Cc, Dd, boys, qthr, total, kmax, cart);
         cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
         f = 1.0;
         if (sa == sb) f *= 0.5;
@@ -475,6 +489,7 @@ __global__ void __launch_bounds__(128) jk_kernel(Pairs P, Shells S, Reps R_, con
     if ((threadIdx.x & 31) == 0 && nq) {
         atomicAdd(cnt, (unsigned long long)nq);
         atomicAdd(cnt + 1, (unsigned long long)np);
+        atomicAdd(R_.qrep + 2 * r + (sizeof(R) == 4 ? 1 : 0), (unsigned long long)nq);
     }
     const int N = R_.nbf[r];
     const size_t off = R_.moff[r];
@@ -507,7 +522,7 @@ __global__ void __launch_bounds__(128) schwarz_kernel(Pairs P, Shells S, const i
     constexpr int NCART = ncart(C::LA) * ncart(C::LB) * ncart(C::LC) * ncart(C::LD);
     double cart[NCART], tmp[NCART];
     const float qone[PIMD_MAXPP] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
-    quartet_cart<C, double>(sbra_l, qone, np, P, ab, A, B, A, B, boys, 0.0f, cart);
+    quartet_cart<C, double>(sbra_l, qone, np, P, ab, A, B, A, B, boys, 0.0f, np * P.npp[ab], np * P.npp[ab], cart);
     cart_to_sph4<C::LA, C::LB, C::LC, C::LD>(cart, tmp);
     constexpr int na = nsph(C::LA), nb = nsph(C::LB);
     double m = 0.0;

@@ -26,6 +26,7 @@ generator is pure Python and deterministic.
 from __future__ import annotations
 
 import itertools
+import heapq
 import sys
 
 LMAX = 2  # s, p, d shells
@@ -506,6 +507,13 @@ def encode_vrr_levels(ops, lv):
     return out
 
 
+def encode_acc(op):
+    """One accumulation op {dst | src << 14 | weight << 28}."""
+    dst, src, w, _ = op
+    assert max(dst, src) < (1 << 14) and 0 <= w < 4
+    return dst | (src << 14) | (w << 28)
+
+
 def encode_hrr(op):
     kind, d, s1, s2, _, _, _, i = op
     assert max(d, s1, s2) < 65536
@@ -541,6 +549,42 @@ def _sort_levels(ops, base_level):
             cur += 1
     offs.append(len(out))
     return [o for _, o in out], offs
+
+
+def _compact_slots(ops, lv, keep, lo):
+    """Shared-memory slots of the work nodes (ids >= lo, written by the
+    level-sorted ops) reassigned by liveness: a node's slot is released once
+    the last level that reads it has passed (the levels are separated by a
+    barrier), and a level's results take the lowest released slots. Nodes in
+    keep stay live to the end (read after the tape). Returns (ops, id map,
+    one past the highest slot)."""
+    last = {}
+    for a in range(len(lv) - 1):
+        for op in ops[lv[a]:lv[a + 1]]:
+            for x in op[2:7]:
+                if x >= lo:
+                    last[x] = a
+    end = len(lv)
+    for x in keep:
+        if x >= lo:
+            last[x] = end
+    free, top, mp = [], lo, {}
+    release = {}
+    for a in range(len(lv) - 1):
+        for x in release.pop(a, []):
+            heapq.heappush(free, x)
+        for op in ops[lv[a]:lv[a + 1]]:
+            d = op[1]
+            slot = heapq.heappop(free) if free else top
+            if slot == top:
+                top += 1
+            mp[d] = slot
+            # a node nobody reads is released after its own level
+            release.setdefault(last.get(d, a) + 1, []).append(slot)
+    out = []
+    for op in ops:
+        out.append((op[0], mp[op[1]]) + tuple(mp.get(x, x) if x >= lo else x for x in op[2:7]) + (op[7],))
+    return out, mp, top
 
 
 def gen_coop(c, grad):
@@ -607,7 +651,9 @@ def gen_coop(c, grad):
             for jf, f in enumerate(fs):
                 accops.append((acc_base[name] + ie * len(fs) + jf, get(e, f, 0), wsel[w], 0))
     vrr_ops, vrr_lv = _sort_levels(ops, {F0 + m: 0 for m in range(L + 1)})
-    nwork = nxt[0] - F0
+    vrr_ops, vmap, vtop = _compact_slots(vrr_ops, vrr_lv, {a[1] for a in accops}, F0 + L + 1)
+    accops = [(a[0], vmap.get(a[1], a[1]), a[2], a[3]) for a in accops]
+    nwork = vtop - F0
     # HRR tapes: the class itself (energy) or the six shifted classes (gradient)
     targets = grad_hrrs(c) if grad else [("E", c, "acc")]
     hrrs = []
@@ -645,8 +691,10 @@ def gen_coop(c, grad):
 
         outs = [hget(a, b, cc, dd) for a in carts(a_) for b in carts(b_) for cc in carts(c_) for dd in carts(d_)]
         sops, slv = _sort_levels(hops, {})
+        sops, hmap, htop = _compact_slots(sops, slv, set(outs), F0)
+        outs = [hmap.get(o, o) if o >= F0 else o for o in outs]
         hrrs.append((hname, sops, slv, outs))
-        nwork = max(nwork, hn[0] - F0)
+        nwork = max(nwork, htop - F0)
     return dict(L=L, nacc=nacc, F0=F0, nwork=nwork, vrr=vrr_ops, vrr_lv=vrr_lv, acc=accops, hrrs=hrrs)
 
 
@@ -664,7 +712,7 @@ def coop_header(nm, grad, t):
            "#pragma once\n\n"]
     out.append(arr(f"{pre}_vrr", [x for w in encode_vrr_levels(t["vrr"], t["vrr_lv"]) for x in w]))
     out.append(arr(f"{pre}_vrr_lv", t["vrr_lv"]))
-    out.append(arr(f"{pre}_acc", [x for op in t["acc"] for x in op]))
+    out.append(arr(f"{pre}_acc", [encode_acc(op) for op in t["acc"]]))
     names = []
     for hname, sops, slv, outs in t["hrrs"]:
         out.append(arr(f"{pre}_hrr{hname}", [x for op in sops for x in encode_hrr(op)]))

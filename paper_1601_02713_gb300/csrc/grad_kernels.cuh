@@ -142,7 +142,9 @@ template <class G, typename R>
 __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp, const Tile* __restrict__ tiles,
                                                      const double* __restrict__ Dall, double* __restrict__ grad,
                                                      const R* __restrict__ boys, double tau_lo, double tau_hi,
-                                                     const double* __restrict__ Dsh, double tau_prim, double fxs)
+                                                     const double* __restrict__ Dsh,
+                                                     unsigned long long* __restrict__ cnt, double tau_prim,
+                                                     double fxs)
 {
     constexpr int LA = G::LA, LB = G::LB, LC = G::LC, LD = G::LD;
     __shared__ R sbra[PP_NF][PIMD_MAXPP];
@@ -212,6 +214,27 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
             }
         work = screen(sidx[tid], cd, gam, gthr);
     }
+    // the lane's surviving primitive quartets, walked as one flat sequence
+    // (row-major over (j, i)) for kmax steps, kmax the longest of the warp
+    auto survives = [&](int i, float qpj, float qgj) { return sqg[i] * qpj + sqp[i] * qgj >= gthr; };
+    int total = 0;
+    if (work) {
+        const int nk = P.npp[cd];
+        for (int j = 0; j < nk; j++) {
+            const float qpj = __ldg(P.qp + (size_t)j * P.n + cd), qgj = __ldg(P.qg + (size_t)j * P.n + cd);
+            for (int i = 0; i < nbra; i++) total += survives(i, qpj, qgj);
+        }
+    }
+    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)total);
+    {
+        // executed quartets and primitive quartets (one atomic pair per warp)
+        const unsigned nq = __reduce_add_sync(0xffffffffu, work ? 1u : 0u);
+        const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)total);
+        if ((threadIdx.x & 31) == 0 && nq) {
+            atomicAdd(cnt, (unsigned long long)nq);
+            atomicAdd(cnt + 1, (unsigned long long)np);
+        }
+    }
     if (!work) return;
     const int sc = P.sa[cd], sd = P.sb[cd];
     double A[3], B[3], Cc[3], Dd[3];
@@ -228,12 +251,24 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
     for (int i = 0; i < G::N_accB; i++) accB[i] = R(0);
     for (int i = 0; i < G::N_accC; i++) accC[i] = R(0);
     const int nket = P.npp[cd];
-    for (int j = 0; j < nket; j++) {
-        const float qpj = __ldg(P.qp + (size_t)j * P.n + cd), qgj = __ldg(P.qg + (size_t)j * P.n + cd);
-        R ket[PP_NF];
-        load_ppn(P, cd, j, ket, PP_NF);
-        for (int i = 0; i < nbra; i++) {
-            if (sqg[i] * qpj + sqp[i] * qgj < gthr) continue;
+    int i = 0, j = 0, jl = -1;
+    float qpj = __ldg(P.qp + cd), qgj = __ldg(P.qg + cd);
+    R ket[PP_NF];
+    for (int k = 0; k < kmax; k++) {
+        if (k < total) {
+            // advance to the next surviving primitive quartet (one exists: k < total)
+            while (!survives(i, qpj, qgj)) {
+                if (++i == nbra) {
+                    i = 0;
+                    ++j;
+                    qpj = __ldg(P.qp + (size_t)j * P.n + cd);
+                    qgj = __ldg(P.qg + (size_t)j * P.n + cd);
+                }
+            }
+            if (j != jl) {
+                load_ppn(P, cd, j, ket, PP_NF);
+                jl = j;
+            }
             R bra[PP_NERI];
 #pragma unroll
             for (int f = 0; f < PP_NERI; f++) bra[f] = sbra[f][i];
@@ -244,6 +279,12 @@ __global__ void __launch_bounds__(128) grad2e_kernel(Pairs P, Shells S, Reps Rp,
             G::template vrr<R>(F, g.PA[0], g.PA[1], g.PA[2], g.WP[0], g.WP[1], g.WP[2], g.QC[0], g.QC[1], g.QC[2],
                                g.WQ[0], g.WQ[1], g.WQ[2], g.o2p, g.o2pr, g.o2q, g.o2qr, g.o2pq, accU, accA, accB,
                                accC, R(2) * sbra[PP_EA][i], R(2) * sbra[PP_EB][i], R(2) * ket[PP_EA]);
+            if (++i == nbra && j + 1 < nket) {
+                i = 0;
+                ++j;
+                qpj = __ldg(P.qp + (size_t)j * P.n + cd);
+                qgj = __ldg(P.qg + (size_t)j * P.n + cd);
+            }
         }
     }
     const R AB0 = R(A[0] - B[0]), AB1 = R(A[1] - B[1]), AB2 = R(A[2] - B[2]);

@@ -56,6 +56,7 @@ void class_pair_ls(int cp, int* la, int* lb, int* lc, int* ld);
 // floating-point operations per primitive quartet of class pair cp: the
 // generated recursion plus per-primitive set-up, Boys and prefactor
 long long class_vrr_flops(int cp);
+long long class_grad_flops(int cp);   // per primitive quartet of the gradient
 // Fock build of one class pair: quartets with bound >= max(tau, fp32_tau) in
 // FP64 (D, boys), those in [tau, fp32_tau) in FP32 (Df, boysf); counters
 // cnt[0..1] FP64 quartets / primitive quartets, cnt[2..3] the same in FP32;
@@ -85,10 +86,11 @@ void launch_prim_schwarz(int pair_class, const Pairs& P, const Shells& S, const 
 // the warp-cooperative kernel, 1 the straight-line kernel with bs threads per
 // block (a class with one variant ignores the choice)
 // (tau_prim: primitive quartets with (qg_i qp_j + qp_i qg_j) |Gamma| below it are skipped; 0 none)
+// cnt[0..1]: executed FP64 quartets and primitive quartets, cnt[2..3] FP32
 void launch_grad2e(int cp, const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,
                    const double* D, double* grad, const double* boys, const float* boysf, double tau,
-                   double fp32_tau, const double* Dsh, int variant, int bs, double tau_prim, double fxs,
-                   cudaStream_t st);
+                   double fp32_tau, const double* Dsh, unsigned long long* cnt, int variant, int bs,
+                   double tau_prim, double fxs, cudaStream_t st);
 void grad2e_tapes_upload();   // once per device
 void boys_table_upload(double** dev_tab, float** dev_tabf);
 // FP32 copies for the mixed-precision quartets

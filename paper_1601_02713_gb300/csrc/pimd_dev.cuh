@@ -67,6 +67,7 @@ struct Reps {
     const int* sh0;             // first (global) shell of each replica
     const int* nsh;             // shells per replica
     const long long* dsoff;     // offset of the replica's nsh x nsh shell-pair density bounds
+    unsigned long long* qrep;   // [nrep][2] executed Fock-build quartets per replica: FP64, FP32
 };
 
 // max |M_mn| over the functions of shells (a, b) of replica r (global shell ids)

@@ -102,6 +102,13 @@ struct pimd_ctx {
     };
     std::vector<MO> mo;
     cudaEvent_t ev[8];
+    // the class-pair launches of a Fock build (and of the gradient) are
+    // spread over the context stream and these side streams (fork/join by
+    // events, also inside a captured graph), so that one launch's last wave
+    // overlaps the next launches instead of leaving SMs idle
+    static constexpr int kSide = 3;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
     int nsm = 152;
     pimd_guess* guess_model = nullptr;   // not owned (guess = 2, 3)
     // per class pair: ket width of the quartet tiles (the straight-line
@@ -118,6 +125,10 @@ struct pimd_ctx {
         int full;
     };
     std::vector<std::vector<TraceRow>> trace;
+    // per SCF iteration of the last call: device time of its Fock build (ms,
+    // all replicas) and the shell quartets it executed
+    std::vector<double> fock_ms_it;
+    std::vector<long long> fock_q_it;
 };
 
 static int set_err(pimd_ctx* ctx, int code, const std::string& msg)
@@ -222,6 +233,11 @@ extern "C" int pimd_ctx_create(pimd_ctx** out, int device)
     boys_table_upload(&ctx->boys, &ctx->boysf);
     grad2e_tapes_upload();
     for (int i = 0; i < 8; i++) cudaEventCreate(&ctx->ev[i]);
+    cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < pimd_ctx::kSide; i++) {
+        cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming);
+    }
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
     if (cudaGetLastError() != cudaSuccess) {
         delete ctx;
@@ -245,6 +261,14 @@ extern "C" void pimd_ctx_destroy(pimd_ctx* ctx)
     if (ctx->boys) cudaFree(ctx->boys);
     if (ctx->boysf) cudaFree(ctx->boysf);
     for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < pimd_ctx::kSide; i++) {
+        if (ctx->side[i]) {
+            cudaStreamSynchronize(ctx->side[i]);
+            cudaStreamDestroy(ctx->side[i]);
+        }
+        if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -378,6 +402,17 @@ extern "C" int pimd_last_trace(const pimd_ctx* ctx, int rep, int maxit, double* 
     return (int)t.size();
 }
 
+extern "C" int pimd_last_fock_times(const pimd_ctx* ctx, int maxit, double* ms, long long* quartets)
+{
+    if (!ctx || maxit < 0) return PIMD_EINVAL;
+    const int n = (int)ctx->fock_ms_it.size();
+    for (int k = 0; k < n && k < maxit; k++) {
+        if (ms) ms[k] = ctx->fock_ms_it[k];
+        if (quartets) quartets[k] = ctx->fock_q_it[k];
+    }
+    return n;
+}
+
 extern "C" int pimd_last_stats(const pimd_ctx* ctx, pimd_stats* out)
 {
     if (!ctx || !out) return PIMD_EINVAL;
@@ -405,8 +440,9 @@ struct Batch {
     int maxsh = 0;
     double* Dsh = nullptr;
     std::vector<int> npp;
-    unsigned long long* cnt = nullptr;   // [4 * class pairs]: executed FP64 quartets and primitive
-                                         // quartets, then the same for FP32
+    unsigned long long* cnt = nullptr;   // [4 * 64] per class pair: executed FP64 quartets and primitive
+                                         // quartets, then the same for FP32, of the Fock builds; the
+                                         // next [4 * 64] the same for the two-electron gradient
     // pairs grouped by (rep, class)
     std::vector<int> pa, pb;
     std::vector<int> grp0;   // [nrep * 6 + 1] start of group (rep, X)
@@ -574,9 +610,12 @@ static int setup_batch(pimd_ctx* ctx, Batch& bt, int nrep, const int* natom_of, 
     UPLOAD("nsh_rep", bt.nsh_rep, d_nshr);
     UPLOAD("dsoff", bt.dsoff, d_dsoff);
     ENSURE("Dsh", dso, bt.Dsh);
-    ENSURE("cnt", 4 * 64, bt.cnt);
-    CK(cudaMemsetAsync(bt.cnt, 0, sizeof(unsigned long long) * 4 * 64, ctx->stream));
-    bt.R = Reps{d_nbf, d_moff, d_active, d_sh0, d_nshr, d_dsoff};
+    ENSURE("cnt", 8 * 64, bt.cnt);
+    CK(cudaMemsetAsync(bt.cnt, 0, sizeof(unsigned long long) * 8 * 64, ctx->stream));
+    unsigned long long* d_qrep;
+    ENSURE("qrep", 2 * nrep, d_qrep);
+    CK(cudaMemsetAsync(d_qrep, 0, sizeof(unsigned long long) * 2 * nrep, ctx->stream));
+    bt.R = Reps{d_nbf, d_moff, d_active, d_sh0, d_nshr, d_dsoff, d_qrep};
 
     // pair data, Schwarz factors (unsorted), then sort each group by Q
     int *d_pa, *d_pb, *d_npp;
@@ -863,6 +902,37 @@ static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, co
 // G' += G'(M) over all class pairs for the replicas in the active mask, with
 // the quartets screened by Q_ab Q_cd max|M block| >= tau; those below fp32_tau
 // (if > 0) are evaluated in FP32 from Mf, an FP32 copy of M made here
+// Launch fn(cp, stream) for every class pair with tiles, the k-th on stream
+// k mod (side streams + 1) (0: the context stream), after everything already
+// queued on the context stream; the context stream then waits for all of them.
+template <class Fn>
+static int fan_out_class_pairs(pimd_ctx* ctx, const Batch& bt, Fn&& fn)
+{
+    constexpr int ns = pimd_ctx::kSide + 1;
+    CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
+    bool used[pimd_ctx::kSide] = {};
+    int k = 0;
+    for (int cp = 0; cp < n_class_pairs(); cp++) {
+        if (bt.tiles[cp].empty()) continue;
+        const int j = k++ % ns;
+        cudaStream_t st = ctx->stream;
+        if (j > 0) {
+            st = ctx->side[j - 1];
+            if (!used[j - 1]) {
+                CK(cudaStreamWaitEvent(st, ctx->fork_ev, 0));
+                used[j - 1] = true;
+            }
+        }
+        fn(cp, st);
+    }
+    for (int i = 0; i < pimd_ctx::kSide; i++)
+        if (used[i]) {
+            CK(cudaEventRecord(ctx->join_ev[i], ctx->side[i]));
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[i], 0));
+        }
+    return PIMD_OK;
+}
+
 static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32_tau, const double* M,
                       double tau_prim, double fxs)
 {
@@ -876,12 +946,12 @@ static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32
         launch_to_float(M, Mf, bt.mtot, ctx->stream);
         ctx->stats.kernel_launches++;
     }
-    for (int cp = 0; cp < n_class_pairs(); cp++) {
-        if (bt.tiles[cp].empty()) continue;
+    const int rc = fan_out_class_pairs(ctx, bt, [&](int cp, cudaStream_t st) {
         launch_jk(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), M, Mf, m.G, ctx->boys, ctx->boysf,
-                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->tile_w[cp], tau_prim, fxs, ctx->stream);
+                  tau, fp32_tau, bt.Dsh, bt.cnt + 4 * cp, ctx->tile_w[cp], tau_prim, fxs, st);
         ctx->stats.kernel_launches += fp32_tau > tau ? 2 : 1;
-    }
+    });
+    if (rc) return rc;
     if (fxs > 0) {
         launch_fixed_to_double(m.G, bt.mtot, fxs, ctx->stream);
         ctx->stats.kernel_launches += 2;
@@ -1262,6 +1332,11 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     std::vector<int> mode(nrep, 2), since_full(nrep, 0);
     const int full_every = o->full_every > 0 ? o->full_every : 8;
     ctx->trace.assign(nrep, {});
+    ctx->fock_ms_it.clear();
+    ctx->fock_q_it.clear();
+    // executed quartets of the Fock builds so far (counters [4 * 64]: quartets, primitive quartets, FP64 then FP32)
+    std::vector<unsigned long long> cnt_it(4 * 64);
+    long long fock_q_tot = 0;
     int nactive = nrep;
     const bool graphs = o->use_graphs != 0;
     GraphSeg seg_fock, seg_err, seg_diag;
@@ -1312,12 +1387,21 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         if (rc) return rc;
         CK(cudaMemcpyAsync(E.data(), m.E, sizeof(double) * nrep, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaMemcpyAsync(emax.data(), m.emax, sizeof(double) * nrep, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(cnt_it.data(), bt.cnt, sizeof(unsigned long long) * cnt_it.size(), cudaMemcpyDeviceToHost,
+                           ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         CK(cudaGetLastError());
+        {
+            long long tot = 0;
+            for (size_t k = 0; k < cnt_it.size(); k += 2) tot += (long long)cnt_it[k];
+            ctx->fock_q_it.push_back(tot - fock_q_tot);
+            fock_q_tot = tot;
+        }
         {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
             ctx->stats.ms_fock += ms;
+            ctx->fock_ms_it.push_back(ms);
         }
         bool anyfin = false;
         for (int r = 0; r < nrep; r++) {
@@ -1402,14 +1486,15 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
         }
         CK(cudaEventRecord(ctx->ev[4], ctx->stream));
         launch_shell_bounds(bt.S, bt.R, nrep, bt.maxsh, m.D, bt.Dsh, nullptr, ctx->stream);
-        for (int cp = 0; cp < n_class_pairs(); cp++) {
-            if (bt.tiles[cp].empty()) continue;
+        const int rcg = fan_out_class_pairs(ctx, bt, [&](int cp, cudaStream_t st) {
             launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_grad, ctx->boys,
-                          ctx->boysf, o->schwarz_tau * 1e-2, o->fp32_tau, bt.Dsh, ctx->grad_var[cp],
-                          ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, o->schwarz_tau * 1e-2 * o->prim_screen,
-                          fx_grad, ctx->stream);
+                          ctx->boysf, o->schwarz_tau * 1e-2, o->fp32_tau, bt.Dsh, bt.cnt + 4 * 64 + 4 * cp,
+                          ctx->grad_var[cp],
+                          ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128, o->schwarz_tau * o->prim_screen,
+                          fx_grad, st);
             ctx->stats.kernel_launches += o->fp32_tau > 0 ? 2 : 1;
-        }
+        });
+        if (rcg) return rcg;
         CK(cudaEventRecord(ctx->ev[5], ctx->stream));
         if (fx_grad > 0) launch_fixed_to_double(d_grad, natot * 3, fx_grad, ctx->stream);
         ctx->stats.kernel_launches += fx_grad > 0 ? 4 : 3;
@@ -1455,10 +1540,10 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     ctx->stats.nquartets_total = bt.nquart;
     {
         // executed work of all Fock builds of the call, from the device counters
-        std::vector<unsigned long long> cnt(4 * 64);
+        std::vector<unsigned long long> cnt(8 * 64);
         CK(cudaMemcpy(cnt.data(), bt.cnt, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
-        double fl = 0.0, er = 0.0, fl32 = 0.0, er32 = 0.0;
-        long long q64 = 0, q32 = 0;
+        double fl = 0.0, er = 0.0, fl32 = 0.0, er32 = 0.0, gfl = 0.0, gfl32 = 0.0;
+        long long q64 = 0, q32 = 0, gq = 0;
         for (int cp = 0; cp < n_class_pairs(); cp++) {
             int la, lb, lc, ld;
             class_pair_ls(cp, &la, &lb, &lc, &ld);
@@ -1469,7 +1554,14 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             er32 += (double)cnt[4 * cp + 2] * nfun;
             q64 += (long long)cnt[4 * cp];
             q32 += (long long)cnt[4 * cp + 2];
+            const unsigned long long* gc = cnt.data() + 4 * 64 + 4 * cp;
+            gfl += (double)gc[1] * class_grad_flops(cp);
+            gfl32 += (double)gc[3] * class_grad_flops(cp);
+            gq += (long long)(gc[0] + gc[2]);
         }
+        ctx->stats.grad_flops = gfl;
+        ctx->stats.grad_flops32 = gfl32;
+        ctx->stats.grad_quartets = gq;
         const int nb = std::max(1, ctx->stats.fock_builds);
         ctx->stats.eri_flops_per_build = fl / nb;
         ctx->stats.eri_flops32_per_build = fl32 / nb;
@@ -1480,6 +1572,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
     }
     std::vector<int> jnc(nrep);
     CK(cudaMemcpy(jnc.data(), m.jnc, sizeof(int) * nrep, cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> qrep(2 * (size_t)nrep);
+    CK(cudaMemcpy(qrep.data(), bt.R.qrep, sizeof(unsigned long long) * qrep.size(), cudaMemcpyDeviceToHost));
     bool allconv = true;
     for (int r = 0; r < nrep; r++) {
         if (jnc[r]) conv[r] = 0;   // a diagonalisation of the replica did not converge
@@ -1489,6 +1583,8 @@ static int run_batch(pimd_ctx* ctx, int nrep, const int* natom_of, const int* Zc
             info[r].final_dE = fdE[r];
             info[r].final_error = ferr[r];
             info[r].nquartets = bt.nquart_rep[r];
+            info[r].nq_fp64 = (long long)qrep[2 * r];
+            info[r].nq_fp32 = (long long)qrep[2 * r + 1];
         }
         allconv = allconv && conv[r];
     }
@@ -1764,9 +1860,10 @@ extern "C" int pimd_autotune(pimd_ctx* ctx, int nrep, int natom, const int* Z, c
                     use[cp] = (v == 0 ? grad_pair_coop(cp) : grad_pair_straight(cp)) && !bt.tiles[cp].empty();
                 rc2 = timed(gms, 2, v, use, [&](int cp) {
                     launch_grad2e(cp, bt.P, bt.S, bt.R, bt.d_tiles[cp], (int)bt.tiles[cp].size(), m.D, d_g,
-                                  ctx->boys, ctx->boysf, o.schwarz_tau * 1e-2, o.fp32_tau, bt.Dsh, v,
+                                  ctx->boys, ctx->boysf, o.schwarz_tau * 1e-2, o.fp32_tau, bt.Dsh,
+                                  bt.cnt + 4 * 64 + 4 * cp, v,
                                   ctx->tile_w[cp] > 0 ? ctx->tile_w[cp] : 128,
-                                  o.schwarz_tau * 1e-2 * o.prim_screen, 0.0, ctx->stream);
+                                  o.schwarz_tau * o.prim_screen, 0.0, ctx->stream);
                 });
             }
         }

@@ -33,7 +33,8 @@ class PimdScfOpts(ctypes.Structure):
 
 class PimdInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("final_dE", ctypes.c_double),
-                ("final_error", ctypes.c_double), ("nquartets", ctypes.c_longlong)]
+                ("final_error", ctypes.c_double), ("nquartets", ctypes.c_longlong),
+                ("nq_fp64", ctypes.c_longlong), ("nq_fp32", ctypes.c_longlong)]
 
 
 class PimdStats(ctypes.Structure):
@@ -42,7 +43,8 @@ class PimdStats(ctypes.Structure):
                 ("nquartets_total", ctypes.c_longlong), ("eri_flops_per_build", ctypes.c_double),
                 ("eris_per_build", ctypes.c_double), ("eri_flops32_per_build", ctypes.c_double),
                 ("quartets_fp64", ctypes.c_longlong), ("quartets_fp32", ctypes.c_longlong),
-                ("eris32_per_build", ctypes.c_double)]
+                ("eris32_per_build", ctypes.c_double), ("grad_flops", ctypes.c_double),
+                ("grad_flops32", ctypes.c_double), ("grad_quartets", ctypes.c_longlong)]
 
 
 class PimdError(RuntimeError):
@@ -89,6 +91,7 @@ def load(path: str | None = None):
     lib.pimd_screened_quartets.argtypes = [_P, ctypes.c_int, _I, _I, _D, _P, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_longlong)]
     lib.pimd_last_trace.argtypes = [_P, ctypes.c_int, ctypes.c_int, _D, _D, _I]
+    lib.pimd_last_fock_times.argtypes = [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong)]
     lib.pimd_fock_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I, _D, _P, ctypes.c_double, ctypes.c_double, _P, _P]
     lib.pimd_one_electron.argtypes = [_P, ctypes.c_int, _I, _D, _P, _D, _D, _D]
     lib.pimd_boys_dev.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
@@ -220,7 +223,7 @@ class Basis:
 
 def _infos(arr):
     return [dict(iterations=i.iterations, converged=i.converged, final_dE=i.final_dE, final_error=i.final_error,
-                 nquartets=i.nquartets) for i in arr]
+                 nquartets=i.nquartets, nq_fp64=i.nq_fp64, nq_fp32=i.nq_fp32) for i in arr]
 
 
 def pimd_bo_forces(ctx: Context, basis: Basis, Z, coords, opts: PimdScfOpts | None = None, check=True):
@@ -377,6 +380,18 @@ def pimd_last_trace(ctx: Context, rep: int) -> dict:
     E, err, full = np.zeros(max(n, 1)), np.zeros(max(n, 1)), np.zeros(max(n, 1), np.int32)
     lib.pimd_last_trace(ctx.handle, int(rep), n, _dp(E), _dp(err), _ip(full))
     return {"energy": E[:n], "error": err[:n], "full_build": full[:n]}
+
+
+def pimd_last_fock_times(ctx: Context) -> dict:
+    """Per SCF iteration of the last forces call: device time (ms) of the
+    Fock build and the shell quartets it executed."""
+    lib = load()
+    n = lib.pimd_last_fock_times(ctx.handle, 0, None, None)
+    if n < 0:
+        raise PimdError(n, "pimd_last_fock_times")
+    ms, q = np.zeros(max(n, 1)), np.zeros(max(n, 1), np.int64)
+    lib.pimd_last_fock_times(ctx.handle, n, _dp(ms), q.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    return {"ms": ms[:n], "quartets": q[:n]}
 
 
 def pimd_last_stats(ctx: Context) -> dict:

@@ -221,6 +221,11 @@ def test_mixed_precision_fp32_quartets(ctx, spd):
     assert rc == 0
     st = native.pimd_last_stats(ctx)
     assert st["quartets_fp32"] > 0
+    # per-replica split of the executed quartets: every replica routes some
+    # to FP32, and the records add up to the call's counters
+    assert all(i["nq_fp32"] > 0 and i["nq_fp64"] > 0 for i in info)
+    assert sum(i["nq_fp32"] for i in info) == st["quartets_fp32"]
+    assert sum(i["nq_fp64"] for i in info) == st["quartets_fp64"]
     assert np.abs(E32 - E64).max() < 1e-7
     assert np.abs(G32 - G64).max() < 1e-6
     for k in range(len(Xs)):
@@ -320,6 +325,47 @@ def test_graph_replay_matches_plain_launches(ctx, spd):
     assert [i["iterations"] for i in i0] == [i["iterations"] for i in i1]
     np.testing.assert_allclose(E1, E0, atol=1e-10, rtol=0)
     np.testing.assert_allclose(G1, G0, atol=1e-9, rtol=0)
+
+
+def test_scf_trace_and_fock_times_are_consistent(ctx, spd):
+    """The per-iteration records of a call agree with its statistics and with
+    the rules of the SCF loop: one trace row per iteration of each replica,
+    the first build and the converging one full, the accepted step within
+    the energy bar, one Fock record per iteration of the longest replica,
+    their times summing to the call's Fock time and their quartets to the
+    executed quartets; the last incremental build, whose density change is
+    small, executes fewer quartets than the full first build (the early
+    ones need not: the change of a start density can be as large as the
+    density)."""
+    bas, B = spd
+    r, _ = inputs.workload("water8_spd_32beads", nrep=3)
+    Z, X = r.stacked()
+    ctx.clear_guess()
+    E, G, info, rc = native.pimd_bo_forces(ctx, B, Z, X, native.scf_opts())
+    assert rc == 0
+    st = native.pimd_last_stats(ctx)
+    for k, inf in enumerate(info):
+        tr = native.pimd_last_trace(ctx, k)
+        assert len(tr["energy"]) == inf["iterations"]
+        assert tr["full_build"][0] == 1 and tr["full_build"][-1] == 1
+        assert tr["energy"][-1] == pytest.approx(E[k], abs=1e-12)
+        assert abs(tr["energy"][-1] - tr["energy"][-2]) < 1e-10
+        assert tr["error"][-1] < 1e-8
+    ft = native.pimd_last_fock_times(ctx)
+    assert len(ft["ms"]) == max(i["iterations"] for i in info) == st["fock_builds"]
+    assert np.all(ft["ms"] > 0)
+    assert ft["ms"].sum() == pytest.approx(st["ms_fock"], rel=1e-6)
+    assert ft["quartets"].sum() == st["quartets_fp64"] + st["quartets_fp32"]
+    assert 0 < ft["quartets"][0] <= st["nquartets_total"]
+    assert sum(i["nq_fp64"] for i in info) == st["quartets_fp64"] and all(i["nq_fp32"] == 0 for i in info)
+    assert all(0 < i["nq_fp64"] <= i["iterations"] * i["nquartets"] for i in info)
+    tr0 = native.pimd_last_trace(ctx, 0)
+    inc = [k for k in range(1, len(tr0["full_build"])) if tr0["full_build"][k] == 0]
+    assert inc and ft["quartets"][inc[-1]] < ft["quartets"][0]
+    # the gradient's executed work: every quartet at most once, and a
+    # recursion of at least one operation per primitive quartet
+    assert 0 < st["grad_quartets"] <= st["nquartets_total"]
+    assert st["grad_flops"] > st["grad_quartets"] and st["grad_flops32"] == 0
 
 
 @pytest.mark.parametrize("fp32_tau", [0.0, 1e-6])
