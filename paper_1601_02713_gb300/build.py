@@ -79,14 +79,12 @@ def _coop_upload_code(nm, grad, g):
              "    cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice);", "    return d;", "}",
              f"static void coop_tape_{nm}(CoopTape& t, int& W, size_t& bytes, int& Wf, size_t& bytesf)", "{",
              "    int dev = 0;", "    cudaGetDevice(&dev);",
-             f"    const int per = coop_warp_doubles({st}::NACC, {st}::NWORK, {st}::L, {nc4});",
-             "    // warps per block (1..4, the kernels' launch bound): the count that puts",
-             "    // the most warps on an SM within its 228 KB of shared memory (227 KB",
-             "    // per block, 1 KB reserved per block); ties go to the larger block",
-             "    W = coop_best_warps((size_t)per * sizeof(double));",
-             "    bytes = (size_t)W * per * sizeof(double);",
-             "    Wf = coop_best_warps((size_t)per * sizeof(float));",
-             "    bytesf = (size_t)Wf * per * sizeof(float);",
+             "    // warps per block (1..4): the count that puts the most warps on an SM",
+             "    // within its shared memory (one workspace per block)",
+             f"    W = coop_best_warps({st}::NACC, {st}::NWORK, {st}::L, {nc4}, sizeof(double));",
+             f"    bytes = (size_t)coop_block_elems({st}::NACC, {st}::NWORK, {st}::L, {nc4}, 32 * W) * sizeof(double);",
+             f"    Wf = coop_best_warps({st}::NACC, {st}::NWORK, {st}::L, {nc4}, sizeof(float));",
+             f"    bytesf = (size_t)coop_block_elems({st}::NACC, {st}::NWORK, {st}::L, {nc4}, 32 * Wf) * sizeof(float);",
              "    if (dev >= 0 && dev < 64 && !g_coop_up[dev]) {",
              "        CoopTape c{};",
              f"        c.vrr = coop_copy({pre}_vrr, sizeof({pre}_vrr) / sizeof(int));",
