@@ -540,7 +540,7 @@ def main():
             "autotune": {"fock_kernel": widths, "grad_kernel": grad_var, "fock_build_ms": tune_ms,
                          "seconds": t_tune,
                          "note": ("per class pair, picked before the warm-up (not timed): Fock ket-tile width "
-                                  "32/64/128 or 0 = warp-cooperative kernel; gradient 0 = warp-cooperative, "
+                                  "32/64/128 or 0 = cooperative kernel; gradient 0 = cooperative, "
                                   "1 = straight-line")},
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -245,7 +245,7 @@ int pimd_boys_dev(pimd_ctx* ctx, int n, int m, const double* T_dev, double* F_de
 /* pimd_boys_f32_dev: the same function in the FP32 evaluation of the
  *   mixed-precision quartets (float T_dev[n] -> float F_dev[n], 0 <= m <= 12);
  *   variant 0 is the compile-time-order form of the straight-line ERI
- *   kernels, 1 the runtime-order form of the warp-cooperative kernels. */
+ *   kernels, 1 the runtime-order form of the cooperative kernels. */
 int pimd_boys_f32_dev(pimd_ctx* ctx, int n, int m, const float* T_dev, float* F_dev, int variant);
 /* pimd_sad_atomic_density: the atomic density of element Z used by the SAD
  * guess (guess = 4, 5), host array D[n][n], n = functions of Z in the basis. */
@@ -366,7 +366,7 @@ int pimd_bf16_gemm_dev(int M, int N, int K, const void* A, int lda, int ta, cons
  * split): per quartet class pair, times the Fock build of the given replicas
  * (SAD density, the options' thresholds) with every generated kernel variant
  * (straight-line kernel with ket tiles of 32, 64 or 128 quartets per block;
- * warp-cooperative tape kernel) and then the gradient with each of its
+ * cooperative tape kernel) and then the gradient with each of its
  * variants, and keeps the fastest in the context; later calls on the context
  * use them. widths[64] (may be NULL): widths[cp] = the Fock choice (32, 64,
  * 128, or 0 for the cooperative kernel), widths[32 + cp] = the gradient choice

@@ -134,7 +134,7 @@ def generate_sources():
         if coop_e[nm]:
             e += _coop_upload_code(nm, False, g)
         # bs > 0: straight-line kernel with bs threads per block; bs == 0: the
-        # warp-cooperative tape kernel
+        # cooperative tape kernel
         e += [f"void launch_jk_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
               "                     const double* D, const float* Df, double* G, const double* boys,",
               "                     const float* boysf, double tau, double fp32_tau, const double* Dsh,",
@@ -185,7 +185,7 @@ def generate_sources():
             gl.append(f"void grad2e_upload_{nm}() {{ CoopTape t; int W, Wf; size_t b, bf; coop_tape_{nm}(t, W, b, Wf, bf); }}")
         else:
             gl.append(f"void grad2e_upload_{nm}() {{}}")
-        # variant 0: warp-cooperative tape kernel, 1: straight-line kernel with bs threads
+        # variant 0: cooperative tape kernel, 1: straight-line kernel with bs threads
         gl += [f"void launch_grad2e_{nm}(const Pairs& P, const Shells& S, const Reps& R, const Tile* tiles, int ntiles,",
                "                        const double* D, double* grad, const double* boys, const float* boysf,",
                "                        double tau, double fp32_tau, const double* Dsh, unsigned long long* cnt,",

@@ -446,7 +446,7 @@ HRR_NAMES = ["Ap", "Bp", "Cp", "Am", "Bm", "Cm"]
 
 
 # ---------------------------------------------------------------------------
-# Level-scheduled tapes for the warp-cooperative kernels of the largest
+# Level-scheduled tapes for the cooperative kernels of the largest
 # classes: every intermediate lives in shared memory and the ops of one
 # dependency level are independent, so the 32 lanes of a warp execute a level
 # in parallel, with a __syncwarp between levels. Slot layout: [0, NACC)

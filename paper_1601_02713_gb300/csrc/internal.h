@@ -61,7 +61,7 @@ long long class_grad_flops(int cp);   // per primitive quartet of the gradient
 // FP64 (D, boys), those in [tau, fp32_tau) in FP32 (Df, boysf); counters
 // cnt[0..1] FP64 quartets / primitive quartets, cnt[2..3] the same in FP32;
 // bs = threads per block = the tiles' ket width for the straight-line
-// kernel, bs = 0 for the warp-cooperative kernel (a class with one variant
+// kernel, bs = 0 for the cooperative kernel (a class with one variant
 // ignores the choice)
 // tau_prim: primitive quartets with qp_i qp_j max|D block| below it are skipped (0: none)
 // fxs > 0: G accumulated as fixed-point integers scaled by fxs (deterministic mode, det_add)
@@ -69,7 +69,7 @@ void launch_jk(int cp, const Pairs& P, const Shells& S, const Reps& R, const Til
                const double* D, const float* Df, double* G, const double* boys, const float* boysf, double tau,
                double fp32_tau, const double* Dsh, unsigned long long* cnt, int bs, double tau_prim, double fxs,
                cudaStream_t st);
-// kernel variants generated for a class pair: the warp-cooperative tape
+// kernel variants generated for a class pair: the cooperative tape
 // kernel and the straight-line kernel, for the Fock build and the gradient
 bool class_pair_coop(int cp);
 bool class_pair_straight(int cp);
@@ -83,7 +83,7 @@ void launch_prim_schwarz(int pair_class, const Pairs& P, const Shells& S, const 
                          const double* boys, double* pp, float* qp, float* qg, cudaStream_t st);
 // two-electron gradient of class pair cp: quartets with bound Q_ab Q_cd |Gamma|
 // >= max(tau, fp32_tau) in FP64, those in [tau, fp32_tau) in FP32; variant 0
-// the warp-cooperative kernel, 1 the straight-line kernel with bs threads per
+// the cooperative kernel, 1 the straight-line kernel with bs threads per
 // block (a class with one variant ignores the choice)
 // (tau_prim: primitive quartets with (qg_i qp_j + qp_i qg_j) |Gamma| below it are skipped; 0 none)
 // cnt[0..1]: executed FP64 quartets and primitive quartets, cnt[2..3] FP32

@@ -623,7 +623,7 @@ __global__ void boys_eval_kernel(int n, int m, const double* T, double* F, const
 
 // FP32 evaluation of the mixed-precision quartets: variant 0 the
 // compile-time-order form of the straight-line kernels, 1 the runtime-order
-// form of the warp-cooperative kernels
+// form of the cooperative kernels
 template <int L>
 __device__ __forceinline__ float boys_f32_fixed(float t, const float* boysf)
 {

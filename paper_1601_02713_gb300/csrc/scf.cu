@@ -112,8 +112,8 @@ struct pimd_ctx {
     int nsm = 152;
     pimd_guess* guess_model = nullptr;   // not owned (guess = 2, 3)
     // per class pair: ket width of the quartet tiles (the straight-line
-    // Fock kernel's block size), 0 = the warp-cooperative Fock kernel; and the
-    // gradient variant (0 warp-cooperative, 1 straight-line). Defaults until
+    // Fock kernel's block size), 0 = the cooperative Fock kernel; and the
+    // gradient variant (0 cooperative, 1 straight-line). Defaults until
     // pimd_autotune times the alternatives: 128 / straight where generated.
     int tile_w[64];
     int grad_var[64];
@@ -1750,9 +1750,9 @@ extern "C" int string_images_forces_dev(pimd_ctx* ctx, int nimg, const int* nato
 // testing hooks
 // ---------------------------------------------------------------------------
 // Autotuner: per class pair, the Fock-build kernel (straight-line with ket
-// tiles of 32, 64 or 128 quartets per block, or the warp-cooperative tape
+// tiles of 32, 64 or 128 quartets per block, or the cooperative tape
 // kernel, where generated) and then the gradient kernel (straight-line or
-// warp-cooperative, where both exist) that run this workload fastest. Each
+// cooperative, where both exist) that run this workload fastest. Each
 // candidate is timed with CUDA events around the class pair's launches, the
 // second of two passes, on the SAD density of the given replicas with the
 // options' thresholds.
