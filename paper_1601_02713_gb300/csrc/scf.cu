@@ -899,9 +899,6 @@ static void diag_density(pimd_ctx* ctx, const Batch& bt, Mats& m, ScfPlan& p, co
     ctx->stats.kernel_launches += 2;
 }
 
-// G' += G'(M) over all class pairs for the replicas in the active mask, with
-// the quartets screened by Q_ab Q_cd max|M block| >= tau; those below fp32_tau
-// (if > 0) are evaluated in FP32 from Mf, an FP32 copy of M made here
 // Launch fn(cp, stream) for every class pair with tiles, the k-th on stream
 // k mod (side streams + 1) (0: the context stream), after everything already
 // queued on the context stream; the context stream then waits for all of them.
@@ -933,6 +930,9 @@ static int fan_out_class_pairs(pimd_ctx* ctx, const Batch& bt, Fn&& fn)
     return PIMD_OK;
 }
 
+// G' += G'(M) over all class pairs for the replicas in the active mask, with
+// the quartets screened by Q_ab Q_cd max|M block| >= tau; those below fp32_tau
+// (if > 0) are evaluated in FP32 from Mf, an FP32 copy of M made here
 static int fock_build(pimd_ctx* ctx, Batch& bt, Mats& m, double tau, double fp32_tau, const double* M,
                       double tau_prim, double fxs)
 {
