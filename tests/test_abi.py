@@ -79,6 +79,16 @@ def test_forces_reject_null_context(lib):
     assert rc == native.PIMD_EINVAL
 
 
+def test_diagnostics_reject_null_context(lib):
+    """The per-call records answer PIMD_EINVAL for a missing context or a
+    negative count instead of touching memory (no GPU involved)."""
+    st = native.PimdStats()
+    assert lib.pimd_last_stats(None, ctypes.byref(st)) == native.PIMD_EINVAL
+    assert lib.pimd_last_trace(None, 0, 0, None, None, None) == native.PIMD_EINVAL
+    assert lib.pimd_last_fock_times(None, 0, None, None) == native.PIMD_EINVAL
+    assert lib.pimd_last_fock_times(None, -1, None, None) == native.PIMD_EINVAL
+
+
 def test_generated_sources_are_deterministic():
     g = B._gen_module()
     import tempfile
