@@ -10,7 +10,9 @@ The paper (Sec. 2) defines the computation as the Born-Oppenheimer energy and
 forces of every replica; Sec. 3.1 fixes the integral cutoff (1e-12) and an SCF
 density threshold. It gives no electronic-structure algorithm, so the oracle
 follows the standard closed-shell Roothaan-Hall SCF with Pulay DIIS and the
-standard analytic RHF gradient (see `rhf.py`).
+standard analytic RHF gradient (see `rhf.py`). `dft.py` (imported as
+`oracle.dft`) is the paper's own level of theory, B3LYP, as a plain
+grid-based Kohn-Sham energy; the CUDA library has no counterpart yet.
 """
 from .rhf import (OracleBasis, boys, build, core_guess, eri_block, eri_full,  # noqa: F401
                   jk, nuclear_repulsion, one_electron, rhf_energy_gradient,
