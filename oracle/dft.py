@@ -331,6 +331,19 @@ def xc_energy_matrix(D, phi, grad, w, func=b3lyp_density):
     return E, V
 
 
+def xc_on_grid(ob: R.OracleBasis, D, pts, w, func=b3lyp_density, chunk: int = 20000):
+    """E_xc and V_xc over the grid in blocks of `chunk` points (the basis
+    values of one block at a time), for molecules whose whole table of basis
+    values would not fit in memory; the same sums as xc_energy_matrix."""
+    E, V = 0.0, np.zeros((ob.nbf, ob.nbf))
+    for a in range(0, len(w), chunk):
+        phi, g, _ = ao_values(ob, pts[a:a + chunk])
+        e, v = xc_energy_matrix(D, phi, g, w[a:a + chunk], func)
+        E += e
+        V += v
+    return E, V
+
+
 # ---------------------------------------------------------------------- SCF
 def ks_scf(ob: R.OracleBasis, Z, xyz, grid=None, a0: float = A0, func=b3lyp_density, conv_energy=1e-10,
            conv_error=1e-8, max_iter=100, diis_size=8, tau=1e-12):
@@ -350,13 +363,22 @@ def ks_scf(ob: R.OracleBasis, Z, xyz, grid=None, a0: float = A0, func=b3lyp_dens
     D = R.core_guess(h, X, nocc)
     if func is not None:
         pts, w = grid if grid is not None else molecular_grid(xyz)
-        phi, gphi, _ = ao_values(ob, pts)
+        # basis values kept for the whole SCF when the table is small,
+        # recomputed block by block every iteration otherwise
+        whole = len(w) * ob.nbf <= 8_000_000
+        if whole:
+            phi, gphi, _ = ao_values(ob, pts)
     Fs, es = [], []
     E_prev = None
     converged = False
     for it in range(1, max_iter + 1):
         J, K, _ = R.jk(ob, D, tau)
-        Exc, Vxc = (0.0, np.zeros_like(h)) if func is None else xc_energy_matrix(D, phi, gphi, w, func)
+        if func is None:
+            Exc, Vxc = 0.0, np.zeros_like(h)
+        elif whole:
+            Exc, Vxc = xc_energy_matrix(D, phi, gphi, w, func)
+        else:
+            Exc, Vxc = xc_on_grid(ob, D, pts, w, func)
         F = h + J - 0.5 * a0 * K + Vxc
         E = float(np.sum(D * h) + 0.5 * np.sum(D * J) - 0.25 * a0 * np.sum(D * K)) + Exc + e_nn
         err = X.T @ (F @ D @ S - S @ D @ F) @ X

@@ -154,6 +154,14 @@ def test_ks_matrix_is_the_derivative_of_the_energy(water):
     assert abs((Ep - Em) / (2 * eps) - float(np.sum(V * P))) < 1e-6 * abs(float(np.sum(V * P)))
 
 
+def test_blocked_grid_sums_equal_the_whole(water):
+    D, w, pts = water["D"], water["w"], water["pts"]
+    E0, V0 = dft.xc_energy_matrix(D, water["phi"], water["g"], w)
+    E1, V1 = dft.xc_on_grid(water["ob"], D, pts, w, chunk=7919)
+    assert abs(E1 - E0) < 1e-11 * abs(E0)
+    assert np.abs(V1 - V0).max() < 1e-11 * np.abs(V0).max()
+
+
 def test_full_exact_exchange_without_xc_is_rhf(water):
     res = dft.ks_scf(water["ob"], water["Z"], water["X"], func=None, a0=1.0)
     assert res["converged"]
