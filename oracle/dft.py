@@ -153,14 +153,20 @@ def _pow(x, n):
     return x ** n if n >= 0 else np.zeros_like(x)
 
 
-def ao_values(ob: R.OracleBasis, points, laplacian: bool = False):
+_HESS = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+
+def ao_values(ob: R.OracleBasis, points, laplacian: bool = False, hessian: bool = False):
     """phi [npts, nbf], grad phi [3, npts, nbf] and (laplacian=True) the
-    Laplacian [npts, nbf] of every basis function at the points."""
+    Laplacian [npts, nbf] of every basis function at the points; with
+    hessian=True the third result is instead the second derivatives
+    [6, npts, nbf] in the order xx, xy, xz, yy, yz, zz."""
     pts = np.asarray(points, float)
     npts = len(pts)
     phi = np.zeros((npts, ob.nbf))
     grad = np.zeros((3, npts, ob.nbf))
     lap = np.zeros((npts, ob.nbf)) if laplacian else None
+    hes = np.zeros((6, npts, ob.nbf)) if hessian else None
     f0 = 0
     for s in range(len(ob.l)):
         l = int(ob.l[s])
@@ -177,6 +183,7 @@ def ao_values(ob: R.OracleBasis, points, laplacian: bool = False):
         cv = np.zeros((npts, len(comps)))
         cg = np.zeros((3, npts, len(comps)))
         cl = np.zeros((npts, len(comps)))
+        ch = np.zeros((6, npts, len(comps))) if hessian else None
         for k, n in enumerate(comps):
             mono = _pow(d[:, 0], n[0]) * _pow(d[:, 1], n[1]) * _pow(d[:, 2], n[2])
             cv[:, k] = mono * g0
@@ -195,6 +202,23 @@ def ao_values(ob: R.OracleBasis, points, laplacian: bool = False):
                                  - 2.0 * (2 * i + 1) * _pow(d[:, x], i) * g1
                                  + 4.0 * _pow(d[:, x], i + 2) * g2)
                 cl[:, k] = t
+            if hessian:
+                P = [_pow(d[:, y], n[y]) for y in range(3)]
+                for hi, (x, y) in enumerate(_HESS):
+                    z = 3 - x - y
+                    if x == y:
+                        # d2/dx2 [x^i G] = i(i-1) x^{i-2} G - 2(2i+1) x^i G1 + 4 x^{i+2} G2
+                        i = n[x]
+                        o = [q for q in range(3) if q != x]
+                        ch[hi, :, k] = P[o[0]] * P[o[1]] * (i * (i - 1) * _pow(d[:, x], i - 2) * g0
+                                                            - 2.0 * (2 * i + 1) * _pow(d[:, x], i) * g1
+                                                            + 4.0 * _pow(d[:, x], i + 2) * g2)
+                    else:
+                        # d2/dxdy [x^i y^j G]: (i x^{i-1} - 2a x^{i+1})(j y^{j-1} - 2a y^{j+1}) per primitive
+                        i, j = n[x], n[y]
+                        xm, xp = i * _pow(d[:, x], i - 1), _pow(d[:, x], i + 1)
+                        ym, yp = j * _pow(d[:, y], j - 1), _pow(d[:, y], j + 1)
+                        ch[hi, :, k] = P[z] * (xm * ym * g0 - 2.0 * (xm * yp + xp * ym) * g1 + 4.0 * xp * yp * g2)
         T = _sph_rows(l, ob.spherical)
         nf = T.shape[0]
         phi[:, f0:f0 + nf] = cv @ T.T
@@ -202,8 +226,11 @@ def ao_values(ob: R.OracleBasis, points, laplacian: bool = False):
             grad[x, :, f0:f0 + nf] = cg[x] @ T.T
         if laplacian:
             lap[:, f0:f0 + nf] = cl @ T.T
+        if hessian:
+            for hi in range(6):
+                hes[hi, :, f0:f0 + nf] = ch[hi] @ T.T
         f0 += nf
-    return phi, grad, lap
+    return phi, grad, (hes if hessian else lap)
 
 
 def density_on_grid(D, phi, grad, lap=None):
@@ -407,5 +434,68 @@ def ks_scf(ob: R.OracleBasis, Z, xyz, grid=None, a0: float = A0, func=b3lyp_dens
         eps, Cp = np.linalg.eigh(X.T @ Fbar @ X)
         C = X @ Cp
         D = 2.0 * C[:, :nocc] @ C[:, :nocc].T
+    # one last diagonalisation of F(D): orbitals, D and the energy-weighted W of the gradient
     eps, Cp = np.linalg.eigh(X.T @ F @ X)
-    return dict(energy=E, D=D, F=F, S=S, eps=eps, iterations=it, converged=converged, exc=Exc)
+    C = X @ Cp
+    Co = C[:, :nocc]
+    return dict(energy=E, D=2.0 * Co @ Co.T, W=2.0 * (Co * eps[:nocc]) @ Co.T, C=C, F=F, S=S, eps=eps,
+                iterations=it, converged=converged, exc=Exc)
+
+
+# ------------------------------------------------------------------ gradient
+def _function_atoms(ob: R.OracleBasis):
+    out = []
+    for s_ in range(len(ob.l)):
+        out += [int(ob.atom[s_])] * ob.shell_nbf(s_)
+    return np.array(out)
+
+
+def xc_gradient(ob: R.OracleBasis, natom, D, pts, w, func=b3lyp_density, chunk: int = 20000):
+    """d E_xc / dA on a grid fixed in space (the weights do not move with the
+    atoms): rho and grad rho change only through the basis functions of A,
+    d phi_m / dA = -grad phi_m for m on A, so
+      d rho / dA_x = -2 sum_{m on A} d_x phi_m (D phi)_m,
+      d (d_y rho) / dA_x = -2 sum_{m on A} [d_x d_y phi_m (D phi)_m + d_x phi_m (D d_y phi)_m],
+    and dE_xc/dA_x = INT [f_rho d rho/dA_x + 2 f_sigma grad rho . d grad rho / dA_x]."""
+    torch = _torch()
+    fat = _function_atoms(ob)
+    g = np.zeros((natom, 3))
+    for a in range(0, len(w), chunk):
+        phi, gp, hs = ao_values(ob, pts[a:a + chunk], hessian=True)
+        wk = w[a:a + chunk]
+        rho, grho, _ = density_on_grid(D, phi, gp)
+        keep = rho > RHO_MIN
+        phi, gp, hs, wk, rho, grho = phi[keep], gp[:, keep], hs[:, keep], wk[keep], rho[keep], grho[:, keep]
+        r = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+        s_ = torch.tensor(np.sum(grho ** 2, axis=0), dtype=torch.float64, requires_grad=True)
+        fr, fs = torch.autograd.grad(func(r, s_).sum(), (r, s_), allow_unused=True)
+        fr = fr.numpy() if fr is not None else np.zeros(len(wk))
+        fs = fs.numpy() if fs is not None else np.zeros(len(wk))
+        Dphi = phi @ D                       # (D phi)_m at each point
+        Dg = gp @ D                          # (D d_y phi)_m, [3, p, m]
+        per_m = np.zeros((3, ob.nbf))
+        for x in range(3):
+            drho = -2.0 * gp[x] * Dphi       # per-function pieces of d rho / dA_x
+            acc = (wk * fr) @ drho
+            for y in range(3):
+                hi = _HESS.index((min(x, y), max(x, y)))
+                dgy = -2.0 * (hs[hi] * Dphi + gp[x] * Dg[y])
+                acc += (wk * 2.0 * fs * grho[y]) @ dgy
+            per_m[x] = acc
+        for x in range(3):
+            np.add.at(g[:, x], fat, per_m[x])
+    return g
+
+
+def b3lyp_energy_gradient(basis: dict, Z, xyz, grid=None, tau: float = 1e-12, **kw):
+    """B3LYP energy (Eh) and gradient dE/dR (Eh/bohr) on a grid fixed in space
+    (default: the molecular grid at these coordinates): one-electron terms
+    with the Kohn-Sham W, the two-electron gradient with 20% exact exchange,
+    the XC gradient (xc_gradient) and dV_nn/dR."""
+    ob = R.OracleBasis.build(basis, Z, xyz)
+    pts, w = grid if grid is not None else molecular_grid(xyz)
+    res = ks_scf(ob, Z, xyz, grid=(pts, w), tau=tau, **kw)
+    D, W = res["D"], res["W"]
+    g = (R.grad_1e(ob, Z, xyz, D, W) + R.grad_2e(ob, len(Z), D, tau, kx=A0)
+         + xc_gradient(ob, len(Z), D, pts, w) + R.nuclear_repulsion(Z, xyz)[1])
+    return res["energy"], g, res

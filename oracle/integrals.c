@@ -481,12 +481,14 @@ long long oracle_jk(BASIS_ARGS, const double *D, double tau, double *J, double *
 
 /* ------------------------------------------------------------------------- */
 /* two-electron gradient                                                      */
-/*   g_A += sum_{mnls} [ 1/2 D_mn D_ls - 1/4 D_ml D_ns ] d(mn|ls)/dA           */
+/*   g_A += sum_{mnls} [ 1/2 D_mn D_ls - kx/4 D_ml D_ns ] d(mn|ls)/dA          */
 /* over canonical quartets with weight f = 1/|stabiliser|; summing the bracket */
-/* over the 8 permutations gives 4 D_mn D_ls - D_ml D_ns - D_ms D_nl.          */
-/* Each of the four centres is differentiated explicitly.                     */
+/* over the 8 permutations gives 4 D_mn D_ls - kx (D_ml D_ns + D_ms D_nl).     */
+/* kx = 1 for Hartree-Fock; a hybrid functional's fraction of exact exchange  */
+/* otherwise (0.20 for B3LYP). Each of the four centres is differentiated     */
+/* explicitly.                                                                */
 /* ------------------------------------------------------------------------- */
-void oracle_grad_2e(BASIS_ARGS, int natom, const double *D, double tau, double *grad)
+void oracle_grad_2e_kx(BASIS_ARGS, int natom, const double *D, double tau, double kx, double *grad)
 {
     MAKE_BASIS;
     int ns = bs.nshell;
@@ -571,8 +573,8 @@ void oracle_grad_2e(BASIS_ARGS, int natom, const double *D, double tau, double *
                         for (int i = 0; i < nb_[0]; i++) for (int j = 0; j < nb_[1]; j++)
                         for (int kk = 0; kk < nb_[2]; kk++) for (int m = 0; m < nb_[3]; m++) {
                             int p = off[a] + i, q = off[b] + j, r = off[c] + kk, s2 = off[d] + m;
-                            double gam = 4.0 * D[p * N + q] * D[r * N + s2] - D[p * N + r] * D[q * N + s2]
-                                         - D[p * N + s2] * D[q * N + r];
+                            double gam = 4.0 * D[p * N + q] * D[r * N + s2]
+                                         - kx * (D[p * N + r] * D[q * N + s2] + D[p * N + s2] * D[q * N + r]);
                             s += gam * der[((i * nb_[1] + j) * nb_[2] + kk) * nb_[3] + m];
                         }
                         gt[bs.atom[sh[k]] * 3 + x] += f * s;
@@ -588,6 +590,11 @@ void oracle_grad_2e(BASIS_ARGS, int natom, const double *D, double tau, double *
     }
     free(Q);
     free(off);
+}
+
+void oracle_grad_2e(BASIS_ARGS, int natom, const double *D, double tau, double *grad)
+{
+    oracle_grad_2e_kx(nshell, l, nprim, poff, exps, coefs, cen, atom, spherical, natom, D, tau, 1.0, grad);
 }
 
 /* ------------------------------------------------------------------------- */

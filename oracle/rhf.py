@@ -65,6 +65,7 @@ def _load():
         lib.oracle_jk.argtypes = basis + [dp, ctypes.c_double, dp, dp]
         lib.oracle_jk.restype = ctypes.c_longlong
         lib.oracle_grad_2e.argtypes = basis + [ctypes.c_int, dp, ctypes.c_double, dp]
+        lib.oracle_grad_2e_kx.argtypes = basis + [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
         lib.oracle_one_electron.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.oracle_grad_1e.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -197,10 +198,15 @@ def jk(ob: OracleBasis, D, tau: float = 1e-12):
     return J, K, nq
 
 
-def grad_2e(ob: OracleBasis, natom, D, tau: float = 1e-12):
+def grad_2e(ob: OracleBasis, natom, D, tau: float = 1e-12, kx: float = 1.0):
+    """Two-electron gradient 1/2 sum (D_mn D_ls - kx/2 D_ml D_ns) d(mn|ls)/dA
+    (kx = 1: Hartree-Fock; a hybrid's fraction of exact exchange otherwise)."""
     g = np.zeros((natom, 3))
     D = np.ascontiguousarray(D, float)
-    _load().oracle_grad_2e(*ob.args(), natom, _dp(D), float(tau), _dp(g))
+    if kx == 1.0:
+        _load().oracle_grad_2e(*ob.args(), natom, _dp(D), float(tau), _dp(g))
+    else:
+        _load().oracle_grad_2e_kx(*ob.args(), natom, _dp(D), float(tau), float(kx), _dp(g))
     return g
 
 

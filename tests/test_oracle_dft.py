@@ -4,7 +4,8 @@ overlap and electron count, the basis derivatives against finite
 differences, the uniform-scaling law of the exchange functionals, the
 equality of the two published forms of LYP, LYP's zero for a one-spin
 density and its uniform-density limit, VWN's exact high-density coefficient, the Kohn-Sham matrix as the
-derivative of the energy, and the reduction to RHF at full exact exchange."""
+derivative of the energy, the reduction to RHF at full exact exchange, and
+the analytic gradient against central finite differences of the energy."""
 import math
 
 import numpy as np
@@ -174,6 +175,58 @@ def test_b3lyp_scf_converges_on_a_converged_grid(water):
     res = dft.ks_scf(water["ob"], water["Z"], water["X"], grid=(water["pts"], water["w"]))
     assert res["converged"]
     assert res["energy"] < water["E_rhf"] - 0.1
-    fine = dft.molecular_grid(water["X"], n_rad=110, n_theta=26)
+    fine = dft.molecular_grid(water["X"], n_rad=90, n_theta=22)
     res2 = dft.ks_scf(water["ob"], water["Z"], water["X"], grid=fine)
     assert abs(res2["energy"] - res["energy"]) < 1e-5
+
+
+def _distorted_water():
+    Z, X = inputs.small_molecule("water")
+    return Z, X + np.random.default_rng(11).normal(scale=0.05, size=X.shape)
+
+
+COORDS = [(0, 2), (1, 1), (2, 0)]
+
+
+def test_exact_exchange_fraction_in_the_gradient():
+    """A hybrid without an XC term (F = h + J - kx K/2) pins the two-electron
+    gradient's exact-exchange fraction kx against central differences."""
+    bas = inputs.basis_set("split_spd")
+    Z, X = _distorted_water()
+    kx = 0.5
+    ob = O.OracleBasis.build(bas, Z, X)
+    res = dft.ks_scf(ob, Z, X, func=None, a0=kx, conv_energy=1e-12, conv_error=1e-10)
+    g = (O.grad_1e(ob, Z, X, res["D"], res["W"]) + O.grad_2e(ob, len(Z), res["D"], kx=kx)
+         + O.nuclear_repulsion(Z, X)[1])
+    h = 1e-4
+    for a, x in COORDS:
+        E = []
+        for sgn in (1, -1):
+            Xs = X.copy()
+            Xs[a, x] += sgn * h
+            E.append(dft.ks_scf(O.OracleBasis.build(bas, Z, Xs), Z, Xs, func=None, a0=kx,
+                                conv_energy=1e-12, conv_error=1e-10)["energy"])
+        assert abs((E[0] - E[1]) / (2 * h) - g[a, x]) < 2e-7, (a, x)
+    # kx = 1 is the Hartree-Fock gradient itself
+    np.testing.assert_allclose(O.grad_2e(ob, len(Z), res["D"], kx=1.0), O.grad_2e(ob, len(Z), res["D"]),
+                               rtol=0, atol=1e-14)
+
+
+def test_b3lyp_gradient_against_finite_differences():
+    """The B3LYP gradient (one-electron terms with the Kohn-Sham W, 20% exact
+    exchange, the XC terms through the basis functions, V_nn) is the
+    derivative of the energy on a grid fixed in space."""
+    bas = inputs.basis_set("split_spd")
+    Z, X = _distorted_water()
+    grid = dft.molecular_grid(X, n_rad=50, n_theta=14)
+    E0, g, res = dft.b3lyp_energy_gradient(bas, Z, X, grid=grid, conv_energy=1e-12, conv_error=1e-10)
+    assert res["converged"]
+    h = 1e-4
+    for a, x in COORDS:
+        E = []
+        for sgn in (1, -1):
+            Xs = X.copy()
+            Xs[a, x] += sgn * h
+            E.append(dft.ks_scf(O.OracleBasis.build(bas, Z, Xs), Z, Xs, grid=grid, conv_energy=1e-12,
+                                conv_error=1e-10)["energy"])
+        assert abs((E[0] - E[1]) / (2 * h) - g[a, x]) < 2e-7, (a, x, (E[0] - E[1]) / (2 * h), g[a, x])
