@@ -1,7 +1,8 @@
 """Pins of the B3LYP oracle (`oracle/dft.py`) against what the mathematics
 fixes, not against itself: the grid's integrals of the oracle's own analytic
 overlap and electron count, the basis derivatives against finite
-differences, the uniform-scaling law of the exchange functionals, the
+differences, the hydrogen atom's local and B88 exchange energies, the
+uniform-scaling law of the exchange functionals, the
 equality of the two published forms of LYP, LYP's zero for a one-spin
 density and its uniform-density limit, VWN's exact high-density coefficient, the Kohn-Sham matrix as the
 derivative of the energy, the reduction to RHF at full exact exchange, and
@@ -134,6 +135,26 @@ def test_vwn_high_density_coefficient(kind):
     assert abs(slope - (1.0 - math.log(2.0)) / math.pi ** 2) < 2e-4
     # correlation lowers the energy at metallic densities
     assert float(dft.vwn_eps(torch.tensor([2.0], dtype=torch.float64), kind)) < 0
+
+
+def test_hydrogen_atom_exchange():
+    """Exchange energies of the hydrogen atom's exact density e^{-2r}/pi (one
+    spin; closed-shell functional on twice the density, halved: the spin
+    scaling of exchange): the local (Dirac-Slater) value in closed form,
+    -(3/2)(3/(4 pi))^{1/3} (27/64) pi^{-1/3} = -0.26804, and Becke's 1988
+    value for B88, -0.3098 hartree (exact: -0.3125)."""
+    pts, w = dft.molecular_grid(np.zeros((1, 3)), n_rad=200, n_theta=8)
+    r = np.linalg.norm(pts, axis=1)
+    rho_a = np.exp(-2.0 * r) / math.pi
+    keep = rho_a > 1e-14
+    rho_a, w = rho_a[keep], w[keep]
+    rho = torch.tensor(2.0 * rho_a, dtype=torch.float64)
+    sigma = torch.tensor((2.0 * 2.0 * rho_a) ** 2, dtype=torch.float64)   # |d rho/dr| = 2 rho
+    e_lda = 0.5 * float(np.sum(w * dft.lda_x(rho).numpy()))
+    e_b88 = 0.5 * float(np.sum(w * (dft.lda_x(rho) + dft.b88_dx(rho, sigma)).numpy()))
+    closed = -1.5 * (3.0 / (4.0 * math.pi)) ** (1.0 / 3.0) * 27.0 / 64.0 * math.pi ** (-1.0 / 3.0)
+    assert abs(e_lda - closed) < 1e-9
+    assert abs(e_b88 - (-0.3098)) < 2e-4
 
 
 def test_b88_is_local_exchange_without_a_gradient():
