@@ -4,7 +4,8 @@ overlap and electron count, the basis derivatives against finite
 differences, the hydrogen atom's local and B88 exchange energies, the
 uniform-scaling law of the exchange functionals, the
 equality of the two published forms of LYP, LYP's zero for a one-spin
-density and its uniform-density limit, VWN's exact high-density coefficient, the Kohn-Sham matrix as the
+density and its uniform-density limit, VWN's exact high-density coefficient
+and the uniform-gas correlation energies VWN5 was fitted to, the Kohn-Sham matrix as the
 derivative of the energy, the reduction to RHF at full exact exchange, and
 the analytic gradient against central finite differences of the energy."""
 import math
@@ -155,6 +156,18 @@ def test_hydrogen_atom_exchange():
     closed = -1.5 * (3.0 / (4.0 * math.pi)) ** (1.0 / 3.0) * 27.0 / 64.0 * math.pi ** (-1.0 / 3.0)
     assert abs(e_lda - closed) < 1e-9
     assert abs(e_b88 - (-0.3098)) < 2e-4
+
+
+def test_vwn5_reproduces_the_uniform_gas_correlation():
+    """VWN's recommended fit reproduces the Ceperley-Alder quantum Monte Carlo
+    correlation energies of the unpolarised uniform gas it was fitted to
+    (hartree per electron; the Perdew-Wang 1992 tabulation of the same
+    data): -0.0600, -0.0448, -0.0281, -0.0185 at rs = 1, 2, 5, 10. The RPA fit
+    lies below them (RPA overestimates correlation)."""
+    for rs, ref in ((1.0, -0.0600), (2.0, -0.0448), (5.0, -0.0281), (10.0, -0.0185)):
+        t = torch.tensor([rs], dtype=torch.float64)
+        assert abs(float(dft.vwn_eps(t, "5")) - ref) < 3e-4, rs
+        assert float(dft.vwn_eps(t, "rpa")) < ref - 0.005
 
 
 def test_b88_is_local_exchange_without_a_gradient():
